@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Throughput of the fused CTU lattice Boltzmann step on GB300.
+
+Workload (default): the sheared cavitating bubble at the paper's largest
+size -- 6144 x 6144 nodes, FP32 shifted storage, CTU2 with the MC limiter,
+T = 0.8, tau = 1e-2, kappa = 1e-4, dt = 1e-4, ds = 1/256, sheared walls at
+gamma_dot dt = 5e-6 (u_w = 0.6), a tanh vapour seed of radius 26 nodes at
+rho_V = 0.23967 in liquid at rho_ext = 1.90, linear initial shear profile.
+One "step" = one fused kernel launch advancing all 6144^2 nodes by dt.
+
+Metric: GLUPS = 1e9 node updates per second (one node update = all 16 f_k
+of one node advanced one step).  Inputs (2 x 2.25 GiB) exceed L2 (129 MB),
+so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank advances its own independent lattice
+(replicas; the step has no exchange), timings are max-reduced.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "sheared-bubble-6144": dict(L=6144, T=0.8, tau=1e-2, rho_ext=1.90, rho_v=0.23967, R=26.0,
+                                W=4.0, shear_dt=5e-6, walls=True, precision="fp32"),
+    "quiescent-bubble-4096": dict(L=4096, T=0.9, tau=1e-3, rho_ext=1.58, rho_v=0.425742, R=20.0,
+                                  W=4.0, shear_dt=0.0, walls=False, precision="fp32",
+                                  reservoir=True),
+    "spinodal-1024-fp64": dict(L=1024, T=0.9, tau=1e-3, rho_ext=1.0, rho_v=1.0, R=0.0, W=0.0,
+                               shear_dt=0.0, walls=False, precision="fp64"),
+}
+METRIC = "GLUPS (16-vel CTU node updates/s) & % HBM roofline"
+DT, DS = 1e-4, 1.0 / 256.0
+
+
+def lib_params(P, w):
+    L = w["L"]
+    p = P.Params(Lx=L, Ly=L, T=w["T"], tau=w["tau"], dt=DT, ds=DS, rho_ext=w["rho_ext"],
+                 precision=P.LBM_FP32_SHIFTED if w["precision"] == "fp32" else P.LBM_FP64,
+                 rho_ref=w["rho_ext"])
+    if w["walls"]:
+        p.boundary = P.LBM_BC_SHEAR_WALLS
+        p.shear_rate = w["shear_dt"] / DT
+    if w.get("reservoir"):
+        p.reservoir = 1
+    return p
+
+
+def initial_fields(w, Lx, Ly):
+    import synth
+    if w["R"] > 0:
+        rho, ux, uy = synth.bubble(Lx, Ly, w["rho_ext"], w["rho_v"], w["R"], w["W"])
+    else:
+        rho, ux, uy = synth.noisy_uniform(Lx, Ly, 1.0, 1e-2, seed=1)
+    if w["walls"]:
+        uw = w["shear_dt"] / DT * Ly * DS / 2.0
+        ux = synth.linear_shear(Lx, Ly, uw)
+    return rho, ux, uy
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("lbm_kernels.cuh", "step_fp32.cu", "step_fp64.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1802_01272_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    e = d.get(workload)
+    if not e or e.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return float(e["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, seconds=15.0):
+    """The FP64 oracle on the host cores, on a bounded sample of the same
+    workload: a 192 x 192 window of the initial state, same physics and
+    boundaries, stepped until ~`seconds` of CPU work."""
+    import oracle as O
+    O.build()
+    n = 192
+    Lx = Ly = w["L"]
+    rho, ux, uy = initial_fields(w, Lx, Ly)
+    cx, cy = Lx // 2 - n // 2, Ly // 2 - n // 2 if not w["walls"] else 0
+    sl = (slice(cy, cy + n), slice(cx, cx + n))
+    op = O.Params(Lx=n, Ly=n, T=w["T"], tau=w["tau"], dt=DT, ds=DS, rho_ext=w["rho_ext"],
+                  boundary=O.BC_SHEAR_WALLS if w["walls"] else O.BC_PERIODIC,
+                  shear_rate=w["shear_dt"] / DT if w["walls"] else 0.0)
+    f = O.init_feq(op, rho[sl].copy(), ux[sl].copy(), uy[sl].copy())
+    O.step(op, f, 1)  # warm-up
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        f = O.step(op, f, 2)
+        steps += 2
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n * n * steps / dt / 1e9, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{n}x{n} window of the {w['L']}^2 workload, FP64 oracle, {steps} steps, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return
+    cb = cpu_baseline(w, seconds=max(5.0, min(20.0, 3.0 * args.steps)))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "GLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "lattice": w["L"], "sample": cb["sample"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "GLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sheared-bubble-6144", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, w, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    import paper_1802_01272_gb300 as P
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    p = lib_params(P, w)
+    rho, ux, uy = initial_fields(w, p.Lx, p.Ly)
+    nodes = p.Lx * p.Ly
+    elem = 4 if p.precision == P.LBM_FP32_SHIFTED else 8
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---------------- device-resident throughput
+    L = P.Lattice(p, stream)
+    d_rho, d_ux, d_uy = (torch.from_numpy(x).cuda() for x in (rho, ux, uy))
+    L.init_rho_u_device(d_rho, d_ux, d_uy)
+    L.step(args.warmup)
+    L.sync()
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    L.step(args.steps)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    L.sync()
+    ms = max_over_ranks(ms)
+    ms_per_step = ms / args.steps
+    value = world * nodes * args.steps / (ms * 1e-3) / 1e9
+
+    # roofline of the step kernel: the only kernel in the timed region
+    peak, peak_kind = load_peaks()
+    alg_bytes = 2 * 16 * elem * nodes
+    achieved = alg_bytes / (ms_per_step * 1e-3) / 1e9
+    traffic = ncu_traffic(args.workload)
+
+    # ---------------- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = [torch.empty(p.Ly, p.Lx, dtype=torch.float64).pin_memory() for _ in range(6)]
+        for t, x in zip(pin[:3], (rho, ux, uy)):
+            t.numpy()[...] = x
+        hr, hx, hy = (t.numpy() for t in pin[:3])
+        orho, oux, ouy = (t.numpy() for t in pin[3:])
+        E = P.Lattice(p, stream)
+        E.init_rho_u(hr, hx, hy)
+        E.step(2)
+        E.diagnostics(threshold=0.5 * (w["rho_ext"] + w["rho_v"]))
+        barrier()
+        t0 = time.perf_counter()
+        E.init_rho_u(hr, hx, hy)
+        for _ in range(args.steps):
+            E.step(1)
+            E.diagnostics(threshold=0.5 * (w["rho_ext"] + w["rho_v"]))
+        E.moments(out=(orho, oux, ouy))
+        barrier()
+        te = max_over_ranks(time.perf_counter() - t0)
+        E.close()
+        diag_bytes = 17 * 8
+        e2e = {"value": world * nodes * args.steps / te / 1e9, "unit": "GLUPS",
+               "h2d_bytes_per_step": int(3 * 8 * nodes / args.steps),
+               "d2h_bytes_per_step": int(diag_bytes + 3 * 8 * nodes / args.steps),
+               "region": "init_rho_u from pinned host + per step (lbm_step(1) + lbm_diagnostics "
+                         "record to host) + final lbm_moments to host"}
+    L.close()
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(w)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if elem == 4 else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "lattice": [p.Lx, p.Ly],
+                       "storage": "fp32 shifted (f - w rho_ref)" if elem == 4 else "fp64",
+                       "scheme": "CTU2 + MC limiter", "T": p.T, "tau": p.tau,
+                       "boundary": "shear walls" if w["walls"] else "periodic",
+                       "l2": "inputs 2x%.2f GiB > L2, no flush" % (16 * elem * nodes / 2**30),
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                         if peak_kind == "measured" else "fallback 6.8 TB/s",
+                         "algorithmic_bytes_per_launch": alg_bytes},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cb,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

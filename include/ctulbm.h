@@ -1,0 +1,159 @@
+/*
+ * ctulbm.h -- C ABI of the GB300 (sm_103a) library for the time step of the
+ * third-order, 16-velocity, isothermal van der Waals lattice Boltzmann model
+ * advanced with corner transport upwind (CTU) schemes, after Sofonea,
+ * Biciusca, Busuioc, Ambrus, Gonnella and Lamura, "Corner transport upwind
+ * lattice Boltzmann model for bubble cavitation" (arXiv:1802.01272).
+ *
+ * One time step (Sec. II C splits Eq. eBGK into two explicit steps):
+ *   1. advection of every f_k over its upwind corner stencil, CTU1
+ *      (Eq. ctueq) or CTU2 (jumps R, MC-limited corrections S, fluxes F, G of
+ *      Sec. II C 2);
+ *   2. on the advected f: rho, u (Sec. II A), the van der Waals acceleration
+ *      g (Eq. eder, vdW pressure Eq. evdw, isotropic 25-point stencil),
+ *      f^eq (Eq. herfeq), F_k (Eq. herforce) and the BGK relaxation
+ *      f <- f - dt/tau (f - f^eq) + dt F_k, optionally regularised (Eq. ereg);
+ *   3. optionally the density reservoir of Sec. III A (rescale f outside R_BC).
+ * Boundaries: periodic, or the sheared permeable walls of Sec. III C (ghost
+ * rows j in {-2,-1} and {Ly, Ly+1} hold f^eq(rho_ext, (-+u_w, 0))), periodic
+ * in x.
+ *
+ * Conventions for every entry point:
+ *  - Return 0 on success or a negative LBM_ERR_* code.  A handle keeps the
+ *    first error of an asynchronous launch (sticky) until lbm_sync() or a
+ *    synchronising call returns it; nothing aborts, traps or exits.
+ *  - Host arrays are FP64, owned by the caller, row-major: scalar fields
+ *    [Ly][Lx] (x fastest), distributions [16][Ly][Lx].  They are read or
+ *    written before the call returns.
+ *  - "_device" variants take FP64 device pointers on the handle's device with
+ *    the same layout; they are stream-ordered on the handle's stream.
+ *  - The library owns all other device memory: allocated in lbm_create,
+ *    freed in lbm_destroy.
+ *  - Velocity order k = 0..15: groups of four with |xi| = (lo,lo), (hi,lo),
+ *    (lo,hi), (hi,hi), lo = sqrt(3 - sqrt 6), hi = sqrt(3 + sqrt 6), weights
+ *    (5+2 sqrt6)/48, 1/48, 1/48, (5-2 sqrt6)/48 (Table I); inside a group the
+ *    signs (+,+), (-,+), (-,-), (+,-).
+ */
+#ifndef CTULBM_H
+#define CTULBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---------------------------------------------------------- */
+#define LBM_OK 0
+#define LBM_ERR_INVALID_ARG (-1)   /* null pointer, bad size or enum value */
+#define LBM_ERR_CFL (-2)           /* max_k |xi_k,a| dt > ds (Sec. II C 1) */
+#define LBM_ERR_DENSITY_RANGE (-3) /* rho outside (0, 1/b) where the EOS is defined */
+#define LBM_ERR_UNSUPPORTED (-4)   /* valid but not built: e.g. another velocity set */
+#define LBM_ERR_OOM (-5)           /* device allocation failed */
+#define LBM_ERR_CUDA (-6)          /* a CUDA runtime call failed */
+#define LBM_ERR_NONFINITE (-7)     /* a step produced rho <= 0 or a non-finite rho */
+#define LBM_ERR_DEVICE_BOUNDS (-8) /* a device-side index check failed (checked builds) */
+#define LBM_ERR_TIMEOUT (-9)       /* a bounded device wait gave up */
+
+/* ---- enumerations ------------------------------------------------------------ */
+#define LBM_VEL_D2Q16_H3 0         /* the 16-velocity third-order set of Table I */
+#define LBM_LIM_MC 0               /* monotonized centred limiter (Sec. II C 2) */
+#define LBM_LIM_ZERO 1             /* Psi = 0: CTU2 reduces to CTU1 (test hook) */
+#define LBM_LIM_ONE 2              /* Psi = 1: unlimited, Lax-Wendroff type (test hook) */
+#define LBM_BC_PERIODIC 0
+#define LBM_BC_SHEAR_WALLS 1       /* Sec. III C */
+#define LBM_FP64 0                 /* f stored and computed in FP64 */
+#define LBM_FP32_SHIFTED 1         /* f - w_k rho_ref stored and computed in FP32 */
+
+/* ---- parameters -------------------------------------------------------------
+ * Defaults (lbm_default_params): a = 9/8, b = 1/3, kappa = 1e-4, T = 0.9,
+ * tau = 1e-3, dt = 1e-4, ds = 1/256, CTU2 with the MC limiter, periodic,
+ * FP32_SHIFTED with rho_ref = 1 (Sec. II D-E and III A).                   */
+typedef struct lbm_params {
+  int32_t Lx, Ly;          /* lattice nodes, each >= 1; FP32 storage with Lx % 4 == 0 is the fast path */
+  int32_t velset;          /* LBM_VEL_D2Q16_H3 */
+  double a, b, kappa, T;   /* p^w = rho T/(1 - b rho) - a rho^2 (Eq. evdw); kappa of Eq. eder; T/T_c */
+  double tau, dt, ds;      /* relaxation time, time step, lattice spacing */
+  int32_t ctu_order;       /* 1 (Eq. ctueq) or 2 (Sec. II C 2) */
+  int32_t limiter;         /* LBM_LIM_* (CTU2 only) */
+  int32_t regularize;      /* 0 or 1: Eq. ereg inside the collision */
+  int32_t boundary;        /* LBM_BC_* */
+  double shear_rate;       /* gamma_dot of Sec. III C; wall speed u_w = gamma_dot Ly ds / 2 */
+  double rho_ext;          /* density of the wall ghost rows and of the reservoir */
+  int32_t reservoir;       /* 0 or 1: after every step, f <- f rho_ext/rho outside
+                              R_BC = min(Lx,Ly)/2 - 1/(2 ds) nodes from (Lx/2, Ly/2) */
+  int32_t precision;       /* LBM_FP64 | LBM_FP32_SHIFTED */
+  double rho_ref;          /* shift of the FP32 storage (ignored in FP64) */
+} lbm_params;
+
+/* Diagnostics record (Sec. III B-C).  Bubble sites are nodes with
+ * rho < threshold (the paper uses (rho_V + rho_L)/2).  Integer sums are exact.
+ * a, b, D, theta follow Eq. (gyr): a = 2 sqrt(Lambda_M), b = 2 sqrt(Lambda_m),
+ * D = (a-b)/(a+b), theta = angle of the major eigenvector to the x axis.      */
+typedef struct lbm_diag {
+  double mass;                 /* sum of rho over the lattice (FP64) */
+  int64_t nb;                  /* bubble sites */
+  int64_t sx, sy;              /* sums of i and j over bubble sites */
+  int64_t sxx, sxy, syy;       /* sums of i*i, i*j, j*j over bubble sites */
+  double rho_center;           /* rho at node (Lx/2, Ly/2) */
+  double rho_ring;             /* mean rho over nodes within 0.5 of distance r_ring from (Lx/2, Ly/2) */
+  double rho_min, rho_max;
+  double cx, cy;               /* bubble centroid (nodes) */
+  double a, b, D, theta;       /* shape from the gyration tensor; 0 if nb < 2 */
+} lbm_diag;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Fill *p with the defaults above for an Lx x Ly lattice. */
+int lbm_default_params(lbm_params* p, int32_t Lx, int32_t Ly);
+
+/* Validate *p (CFL, tau > 0, dt/tau < 2, 0 < rho_ext < 1/b when used, enums),
+ * select the device current on the calling thread, allocate two ping-pong
+ * buffers of 16 Lx Ly values plus small work areas, and bind the handle to
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * The distributions are uninitialised until lbm_init_rho_u or lbm_set_f. */
+int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out);
+
+/* Free every device allocation of the handle (synchronises its stream). NULL is a no-op. */
+void lbm_destroy(lbm_handle* h);
+
+/* f_k = f_k^eq(rho, u) (Eq. herfeq) at every node, from host FP64 fields [Ly][Lx]. */
+int lbm_init_rho_u(lbm_handle* h, const double* rho, const double* ux, const double* uy);
+int lbm_init_rho_u_device(lbm_handle* h, const double* rho, const double* ux, const double* uy);
+
+/* Copy distributions in or out, FP64 [16][Ly][Lx] (converted to/from the storage precision). */
+int lbm_set_f(lbm_handle* h, const double* f);
+int lbm_get_f(lbm_handle* h, double* f);
+int lbm_set_f_device(lbm_handle* h, const double* f);
+int lbm_get_f_device(lbm_handle* h, double* f);
+
+/* Advance n >= 0 steps on the handle's stream (asynchronous; one fused kernel per step). */
+int lbm_step(lbm_handle* h, int64_t n);
+
+/* rho, u = (sum_k f_k, sum_k f_k xi_k / rho) of the current state, FP64 [Ly][Lx].
+ * The host version synchronises the stream. */
+int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy);
+int lbm_moments_device(lbm_handle* h, double* rho, double* ux, double* uy);
+
+/* Reduction of the current state into *out (FP64 accumulators, exact integer sums);
+ * synchronises the stream. */
+int lbm_diagnostics(lbm_handle* h, double threshold, double r_ring, lbm_diag* out);
+
+/* counts[b] = number of nodes with lo + b (hi-lo)/nbins <= rho < lo + (b+1)(hi-lo)/nbins;
+ * 1 <= nbins <= 65536; synchronises the stream. */
+int lbm_histogram(lbm_handle* h, int32_t nbins, double lo, double hi, int64_t* counts);
+
+/* Wait for the handle's stream and return (then clear) its sticky error. */
+int lbm_sync(lbm_handle* h);
+
+/* Number of steps taken since the last init / set. */
+int64_t lbm_step_count(const lbm_handle* h);
+
+/* Static description of a code. */
+const char* lbm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTULBM_H */

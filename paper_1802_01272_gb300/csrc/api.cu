@@ -1,0 +1,521 @@
+// api.cu -- the C ABI declared in include/ctulbm.h.
+//
+// Host-side duties: parameter validation (CFL of Sec. II C 1, density range of
+// Eq. evdw), per-velocity constants in FP64 (Table I, Eqs. ctueq, herfeq,
+// ereg), launch geometry of the persistent step kernel, sticky error state,
+// and the small host finishing step of the diagnostics (eigenvalues of the
+// 2x2 gyration tensor, Eq. gyr).
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "ctulbm.h"
+#include "lbm_internal.h"
+
+using namespace ctulbm;
+
+struct lbm_handle {
+  lbm_params p;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  size_t elem = 4;
+  void* f[2] = {nullptr, nullptr};
+  int cur = 0;
+  unsigned int* d_err = nullptr;
+  DiagAcc* d_acc = nullptr;
+  double* d_work = nullptr;       // 3 planes of FP64 for moments / init staging
+  size_t work_elems = 0;
+  int64_t steps = 0;
+  int sticky = LBM_OK;
+  int grid = 0;
+  long long rows_per_cta = 0;
+  int nstrip = 0;
+  bool vec = false;
+  size_t smem = 0;
+  double xi[16][2], w[16];
+  StepArgs<float> a32;
+  StepArgs<double> a64;
+  AuxArgs aux;
+};
+
+namespace {
+
+void velocity_table(double xi[16][2], double w[16]) {
+  const double s6 = std::sqrt(6.0);
+  const double lo = std::sqrt(3.0 - s6), hi = std::sqrt(3.0 + s6);
+  const double mag[4][2] = {{lo, lo}, {hi, lo}, {lo, hi}, {hi, hi}};
+  const double wt[4] = {(5.0 + 2.0 * s6) / 48.0, 1.0 / 48.0, 1.0 / 48.0, (5.0 - 2.0 * s6) / 48.0};
+  const double sg[4][2] = {{1, 1}, {-1, 1}, {-1, -1}, {1, -1}};
+  for (int m = 0; m < 4; ++m)
+    for (int s = 0; s < 4; ++s) {
+      xi[4 * m + s][0] = sg[s][0] * mag[m][0];
+      xi[4 * m + s][1] = sg[s][1] * mag[m][1];
+      w[4 * m + s] = wt[m];
+    }
+}
+
+// Eq. (herfeq) in FP64 on the host (wall ghost rows).
+void feq_host(const lbm_params& p, const double xi[16][2], const double w[16], double rho,
+              double ux, double uy, double* out) {
+  const double T = p.T, u2 = ux * ux + uy * uy;
+  for (int k = 0; k < 16; ++k) {
+    const double cu = xi[k][0] * ux + xi[k][1] * uy;
+    const double x2 = xi[k][0] * xi[k][0] + xi[k][1] * xi[k][1];
+    out[k] = w[k] * rho *
+             (1.0 + cu + 0.5 * (cu * cu - u2 + (T - 1.0) * (x2 - 2.0)) +
+              cu / 6.0 * (cu * cu - 3.0 * u2 + 3.0 * (T - 1.0) * (x2 - 4.0)));
+  }
+}
+
+int set_err(lbm_handle* h, int code) {
+  if (h && h->sticky == LBM_OK) h->sticky = code;
+  return code;
+}
+
+int cuda_check(lbm_handle* h, cudaError_t e) {
+  if (e == cudaSuccess) return LBM_OK;
+  return set_err(h, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA);
+}
+
+double rho_ref_of(const lbm_params& p) { return p.precision == LBM_FP64 ? 0.0 : p.rho_ref; }
+
+template <typename T>
+void fill_step_args(lbm_handle* h, StepArgs<T>& a) {
+  const lbm_params& p = h->p;
+  const double lam = p.dt / p.ds, om = p.dt / p.tau, rr = rho_ref_of(p);
+  a.Lx = p.Lx;
+  a.Ly = p.Ly;
+  a.plane = (long long)p.Lx * p.Ly;
+  a.nstrip = h->nstrip;
+  a.rows_total = (long long)h->nstrip * p.Ly;
+  a.rows_per_cta = h->rows_per_cta;
+  a.walls = p.boundary == LBM_BC_SHEAR_WALLS;
+  a.reservoir = p.reservoir;
+  a.regularize = p.regularize;
+  a.rho_ref = (T)rr;
+  a.Tt = (T)p.T;
+  a.a = (T)p.a;
+  a.b = (T)p.b;
+  a.kappa = (T)p.kappa;
+  a.inv_ds = (T)(1.0 / p.ds);
+  a.inv_ds2 = (T)(1.0 / (p.ds * p.ds));
+  a.dt = (T)p.dt;
+  a.omega = (T)om;
+  a.one_m_omega = (T)(1.0 - om);
+  a.om2 = (T)(0.5 * om);
+  a.om6 = (T)(om / 6.0);
+  a.rho_ext = (T)p.rho_ext;
+  const int Lmin = p.Lx < p.Ly ? p.Lx : p.Ly;
+  const double rbc = Lmin / 2.0 - 1.0 / (2.0 * p.ds);
+  a.rbc2 = (T)(rbc > 0 ? rbc * rbc : 0.0);
+  a.cxc = (T)(p.Lx / 2.0);
+  a.cyc = (T)(p.Ly / 2.0);
+  a.err = h->d_err;
+  double gb[16], gt[16];
+  const double uw = p.shear_rate * p.Ly * p.ds / 2.0;
+  feq_host(p, h->xi, h->w, p.rho_ext, -uw, 0.0, gb);
+  feq_host(p, h->xi, h->w, p.rho_ext, +uw, 0.0, gt);
+  for (int k = 0; k < 16; ++k) {
+    const double x = h->xi[k][0], y = h->xi[k][1];
+    const double ax = std::fabs(x), ay = std::fabs(y);
+    const double cx = lam * ax, cy = lam * ay;
+    const double hx = 0.5 * ax * (1.0 - cx), hy = 0.5 * ay * (1.0 - cy);
+    const double x2 = x * x + y * y;
+    const double Ak = (p.T - 1.0) * (x2 - 2.0) / 2.0, Bk = (p.T - 1.0) * (x2 - 4.0) / 2.0;
+    VelConst<T>& v = a.v[k];
+    v.xi_x = (T)x;
+    v.xi_y = (T)y;
+    v.w = (T)h->w[k];
+    v.c00 = (T)((1.0 - cx) * (1.0 - cy));
+    v.c10 = (T)(cx * (1.0 - cy));
+    v.c01 = (T)(cy * (1.0 - cx));
+    v.c11 = (T)(cx * cy);
+    // U2 = -lam hx [(1-cy) dS^x + cy dS^x(j - sgn_y)] - lam hy [(1-cx) dS^y + cx dS^y(i - sgn_x)],
+    // with the kernel's half-limited jumps (hence the factor 2)
+    v.a1 = (T)(2.0 * lam * hx * (1.0 - cy));
+    v.a2 = (T)(2.0 * lam * hx * cy);
+    v.b1 = (T)(2.0 * lam * hy * (1.0 - cx));
+    v.b2 = (T)(2.0 * lam * hy * cx);
+    v.omA = (T)(om * Ak);
+    v.Ak = (T)Ak;
+    v.omB = (T)(om * Bk);
+    v.Bk = (T)Bk;
+    v.gbot = (T)(gb[k] - h->w[k] * rr);
+    v.gtop = (T)(gt[k] - h->w[k] * rr);
+    // Eq. (ereg): w [ H2:A2 / 2! + H3:A3 / 3! ] over the independent components
+    v.r2xx = (T)(0.5 * (x * x - 1.0));
+    v.r2xy = (T)(x * y);
+    v.r2yy = (T)(0.5 * (y * y - 1.0));
+    v.r3xxx = (T)((x * x * x - 3.0 * x) / 6.0);
+    v.r3xxy = (T)(0.5 * (x * x * y - y));
+    v.r3xyy = (T)(0.5 * (x * y * y - x));
+    v.r3yyy = (T)((y * y * y - 3.0 * y) / 6.0);
+  }
+}
+
+int validate(const lbm_params* p) {
+  if (!p) return LBM_ERR_INVALID_ARG;
+  if (p->Lx < 1 || p->Ly < 1) return LBM_ERR_INVALID_ARG;
+  if ((long long)p->Lx * p->Ly > (1LL << 31) - 1) return LBM_ERR_INVALID_ARG;
+  if (p->velset != LBM_VEL_D2Q16_H3) return LBM_ERR_UNSUPPORTED;
+  if (p->ctu_order != 1 && p->ctu_order != 2) return LBM_ERR_INVALID_ARG;
+  if (p->limiter < 0 || p->limiter > 2) return LBM_ERR_INVALID_ARG;
+  if (p->boundary != LBM_BC_PERIODIC && p->boundary != LBM_BC_SHEAR_WALLS)
+    return LBM_ERR_INVALID_ARG;
+  if (p->precision != LBM_FP64 && p->precision != LBM_FP32_SHIFTED) return LBM_ERR_UNSUPPORTED;
+  if (p->regularize != 0 && p->regularize != 1) return LBM_ERR_INVALID_ARG;
+  if (p->reservoir != 0 && p->reservoir != 1) return LBM_ERR_INVALID_ARG;
+  if (!(p->tau > 0) || !(p->dt > 0) || !(p->ds > 0) || !(p->T > 0)) return LBM_ERR_INVALID_ARG;
+  if (!(p->dt / p->tau < 2.0)) return LBM_ERR_INVALID_ARG;       // explicit relaxation stability
+  if (!(p->kappa >= 0) || !(p->a >= 0) || !(p->b >= 0)) return LBM_ERR_INVALID_ARG;
+  const double vmax = std::sqrt(3.0 + std::sqrt(6.0));
+  if (vmax * p->dt > p->ds) return LBM_ERR_CFL;                   // Sec. II C 1
+  if (p->boundary == LBM_BC_SHEAR_WALLS || p->reservoir) {
+    if (!(p->rho_ext > 0) || (p->b > 0 && !(p->rho_ext * p->b < 1.0))) return LBM_ERR_DENSITY_RANGE;
+  }
+  if (!std::isfinite(p->shear_rate)) return LBM_ERR_INVALID_ARG;
+  if (p->precision == LBM_FP32_SHIFTED && !std::isfinite(p->rho_ref)) return LBM_ERR_INVALID_ARG;
+  return LBM_OK;
+}
+
+int check_device_error(lbm_handle* h) {
+  unsigned int e = 0;
+  if (cudaMemcpyAsync(&e, h->d_err, sizeof(e), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return set_err(h, LBM_ERR_CUDA);
+  if (e & 1u) set_err(h, LBM_ERR_NONFINITE);
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_default_params(lbm_params* p, int32_t Lx, int32_t Ly) {
+  if (!p) return LBM_ERR_INVALID_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->Lx = Lx;
+  p->Ly = Ly;
+  p->velset = LBM_VEL_D2Q16_H3;
+  p->a = 9.0 / 8.0;
+  p->b = 1.0 / 3.0;
+  p->kappa = 1e-4;
+  p->T = 0.9;
+  p->tau = 1e-3;
+  p->dt = 1e-4;
+  p->ds = 1.0 / 256.0;
+  p->ctu_order = 2;
+  p->limiter = LBM_LIM_MC;
+  p->regularize = 0;
+  p->boundary = LBM_BC_PERIODIC;
+  p->shear_rate = 0.0;
+  p->rho_ext = 1.0;
+  p->reservoir = 0;
+  p->precision = LBM_FP32_SHIFTED;
+  p->rho_ref = 1.0;
+  return LBM_OK;
+}
+
+int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out) {
+  if (!out) return LBM_ERR_INVALID_ARG;
+  *out = nullptr;
+  int v = validate(p);
+  if (v != LBM_OK) return v;
+  lbm_handle* h = new (std::nothrow) lbm_handle();
+  if (!h) return LBM_ERR_OOM;
+  h->p = *p;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return LBM_ERR_CUDA;
+  }
+  h->elem = p->precision == LBM_FP64 ? 8 : 4;
+  velocity_table(h->xi, h->w);
+  const size_t plane = (size_t)p->Lx * p->Ly;
+  const size_t bytes = 16 * plane * h->elem;
+  h->work_elems = 3 * plane;
+  cudaError_t e = cudaSuccess;
+  if ((e = cudaMalloc(&h->f[0], bytes)) != cudaSuccess ||
+      (e = cudaMalloc(&h->f[1], bytes)) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_err, sizeof(unsigned int))) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_acc, sizeof(DiagAcc))) != cudaSuccess) {
+    lbm_destroy(h);
+    return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+  }
+  cudaMemsetAsync(h->d_err, 0, sizeof(unsigned int), h->stream);
+
+  // launch geometry: strips of TW output columns, rows split evenly over a
+  // persistent grid of (SMs x resident CTAs), at least 48 rows per CTA
+  h->nstrip = (p->Lx + TW - 1) / TW;
+  h->vec = (p->Lx % 4) == 0;
+  h->smem = step_smem_bytes(h->elem);
+  const int lim = p->ctu_order == 1 ? 0 : p->limiter;
+  int occ = h->elem == 4 ? step_occupancy_f32(p->ctu_order, lim, h->vec, h->smem)
+                         : step_occupancy_f64(p->ctu_order, lim, h->vec, h->smem);
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+  if (occ < 1 || nsm < 1) {
+    lbm_destroy(h);
+    return LBM_ERR_CUDA;
+  }
+  const long long rows_total = (long long)h->nstrip * p->Ly;
+  long long grid = (long long)nsm * occ;
+  const long long by_rows = (rows_total + 47) / 48;
+  if (grid > by_rows) grid = by_rows;
+  if (grid < 1) grid = 1;
+  h->rows_per_cta = (rows_total + grid - 1) / grid;
+  h->grid = (int)((rows_total + h->rows_per_cta - 1) / h->rows_per_cta);
+
+  if (h->elem == 4)
+    fill_step_args<float>(h, h->a32);
+  else
+    fill_step_args<double>(h, h->a64);
+  AuxArgs& x = h->aux;
+  x.Lx = p->Lx;
+  x.Ly = p->Ly;
+  x.plane = (long long)plane;
+  x.storage64 = h->elem == 8;
+  x.rho_ref = rho_ref_of(*p);
+  x.Tt = p->T;
+  std::memcpy(x.xi, h->xi, sizeof(h->xi));
+  std::memcpy(x.w, h->w, sizeof(h->w));
+  *out = h;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  cudaFree(h->f[0]);
+  cudaFree(h->f[1]);
+  cudaFree(h->d_err);
+  cudaFree(h->d_acc);
+  cudaFree(h->d_work);
+  delete h;
+}
+
+static int ensure_work(lbm_handle* h) {
+  if (h->d_work) return LBM_OK;
+  if (cudaMalloc(&h->d_work, sizeof(double) * h->work_elems) != cudaSuccess)
+    return set_err(h, LBM_ERR_OOM);
+  return LBM_OK;
+}
+
+int lbm_init_rho_u_device(lbm_handle* h, const double* rho, const double* ux, const double* uy) {
+  if (!h || !rho || !ux || !uy) return LBM_ERR_INVALID_ARG;
+  h->cur = 0;
+  h->steps = 0;
+  return cuda_check(h, launch_init_feq(h->aux, h->f[0], rho, ux, uy, h->stream));
+}
+
+int lbm_init_rho_u(lbm_handle* h, const double* rho, const double* ux, const double* uy) {
+  if (!h || !rho || !ux || !uy) return LBM_ERR_INVALID_ARG;
+  int r = ensure_work(h);
+  if (r) return r;
+  const size_t n = (size_t)h->aux.plane, b = n * sizeof(double);
+  double* d = h->d_work;
+  if (cuda_check(h, cudaMemcpyAsync(d, rho, b, cudaMemcpyHostToDevice, h->stream)) ||
+      cuda_check(h, cudaMemcpyAsync(d + n, ux, b, cudaMemcpyHostToDevice, h->stream)) ||
+      cuda_check(h, cudaMemcpyAsync(d + 2 * n, uy, b, cudaMemcpyHostToDevice, h->stream)))
+    return h->sticky;
+  r = lbm_init_rho_u_device(h, d, d + n, d + 2 * n);
+  if (r) return r;
+  return cuda_check(h, cudaStreamSynchronize(h->stream));
+}
+
+int lbm_set_f_device(lbm_handle* h, const double* f) {
+  if (!h || !f) return LBM_ERR_INVALID_ARG;
+  h->cur = 0;
+  h->steps = 0;
+  return cuda_check(h, launch_set_f(h->aux, h->f[0], f, h->stream));
+}
+
+int lbm_get_f_device(lbm_handle* h, double* f) {
+  if (!h || !f) return LBM_ERR_INVALID_ARG;
+  return cuda_check(h, launch_get_f(h->aux, h->f[h->cur], f, h->stream));
+}
+
+// Host transfers stage through a device FP64 buffer of 16 planes, taken from
+// the idle ping-pong buffer when the storage is FP64-sized, else allocated.
+static int with_f64_stage(lbm_handle* h, double** stage, bool* owned) {
+  *owned = false;
+  if (h->elem == 8) {
+    *stage = static_cast<double*>(h->f[1 - h->cur]);
+    return LBM_OK;
+  }
+  if (cudaMalloc(stage, sizeof(double) * 16 * (size_t)h->aux.plane) != cudaSuccess)
+    return set_err(h, LBM_ERR_OOM);
+  *owned = true;
+  return LBM_OK;
+}
+
+int lbm_set_f(lbm_handle* h, const double* f) {
+  if (!h || !f) return LBM_ERR_INVALID_ARG;
+  double* st;
+  bool owned;
+  h->cur = 0;  // the stage may be buffer 1
+  int r = with_f64_stage(h, &st, &owned);
+  if (r) return r;
+  const size_t b = sizeof(double) * 16 * (size_t)h->aux.plane;
+  r = cuda_check(h, cudaMemcpyAsync(st, f, b, cudaMemcpyHostToDevice, h->stream));
+  if (!r) r = lbm_set_f_device(h, st);
+  if (!r) r = cuda_check(h, cudaStreamSynchronize(h->stream));
+  if (owned) cudaFree(st);
+  return r;
+}
+
+int lbm_get_f(lbm_handle* h, double* f) {
+  if (!h || !f) return LBM_ERR_INVALID_ARG;
+  double* st;
+  bool owned;
+  int r = with_f64_stage(h, &st, &owned);
+  if (r) return r;
+  const size_t b = sizeof(double) * 16 * (size_t)h->aux.plane;
+  r = lbm_get_f_device(h, st);
+  if (!r) r = cuda_check(h, cudaMemcpyAsync(f, st, b, cudaMemcpyDeviceToHost, h->stream));
+  if (!r) r = cuda_check(h, cudaStreamSynchronize(h->stream));
+  if (owned) cudaFree(st);
+  return r;
+}
+
+int lbm_step(lbm_handle* h, int64_t n) {
+  if (!h || n < 0) return LBM_ERR_INVALID_ARG;
+  const int lim = h->p.ctu_order == 1 ? 0 : h->p.limiter;
+  for (int64_t s = 0; s < n; ++s) {
+    cudaError_t e;
+    if (h->elem == 4) {
+      h->a32.fin = static_cast<const float*>(h->f[h->cur]);
+      h->a32.fout = static_cast<float*>(h->f[1 - h->cur]);
+      e = launch_step_f32(h->a32, h->p.ctu_order, lim, h->vec, h->grid, h->smem, h->stream);
+    } else {
+      h->a64.fin = static_cast<const double*>(h->f[h->cur]);
+      h->a64.fout = static_cast<double*>(h->f[1 - h->cur]);
+      e = launch_step_f64(h->a64, h->p.ctu_order, lim, h->vec, h->grid, h->smem, h->stream);
+    }
+    if (e != cudaSuccess) return cuda_check(h, e);
+    h->cur ^= 1;
+    h->steps += 1;
+  }
+  return LBM_OK;
+}
+
+int lbm_moments_device(lbm_handle* h, double* rho, double* ux, double* uy) {
+  if (!h || !rho || !ux || !uy) return LBM_ERR_INVALID_ARG;
+  return cuda_check(h, launch_moments(h->aux, h->f[h->cur], rho, ux, uy, h->stream));
+}
+
+int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy) {
+  if (!h || !rho || !ux || !uy) return LBM_ERR_INVALID_ARG;
+  int r = ensure_work(h);
+  if (r) return r;
+  const size_t n = (size_t)h->aux.plane, b = n * sizeof(double);
+  double* d = h->d_work;
+  r = lbm_moments_device(h, d, d + n, d + 2 * n);
+  if (r) return r;
+  if (cuda_check(h, cudaMemcpyAsync(rho, d, b, cudaMemcpyDeviceToHost, h->stream)) ||
+      cuda_check(h, cudaMemcpyAsync(ux, d + n, b, cudaMemcpyDeviceToHost, h->stream)) ||
+      cuda_check(h, cudaMemcpyAsync(uy, d + 2 * n, b, cudaMemcpyDeviceToHost, h->stream)) ||
+      cuda_check(h, cudaStreamSynchronize(h->stream)))
+    return h->sticky;
+  return lbm_sync(h);
+}
+
+int lbm_diagnostics(lbm_handle* h, double threshold, double r_ring, lbm_diag* out) {
+  if (!h || !out) return LBM_ERR_INVALID_ARG;
+  DiagAcc acc;
+  std::memset(&acc, 0, sizeof(acc));
+  acc.rmin_key = ~0ULL;
+  acc.rho_center = NAN;
+  if (cuda_check(h, cudaMemcpyAsync(h->d_acc, &acc, sizeof(acc), cudaMemcpyHostToDevice,
+                                    h->stream)) ||
+      cuda_check(h, launch_diag(h->aux, h->f[h->cur], threshold, r_ring, h->d_acc, h->stream)) ||
+      cuda_check(h, cudaMemcpyAsync(&acc, h->d_acc, sizeof(acc), cudaMemcpyDeviceToHost,
+                                    h->stream)) ||
+      cuda_check(h, cudaStreamSynchronize(h->stream)))
+    return h->sticky;
+  auto unkey = [](unsigned long long k) {
+    unsigned long long b = (k & 0x8000000000000000ULL) ? (k & ~0x8000000000000000ULL) : ~k;
+    double v;
+    std::memcpy(&v, &b, sizeof(v));
+    return v;
+  };
+  std::memset(out, 0, sizeof(*out));
+  out->mass = acc.mass;
+  out->nb = (int64_t)acc.nb;
+  out->sx = (int64_t)acc.sx;
+  out->sy = (int64_t)acc.sy;
+  out->sxx = (int64_t)acc.sxx;
+  out->sxy = (int64_t)acc.sxy;
+  out->syy = (int64_t)acc.syy;
+  out->rho_center = acc.rho_center;
+  out->rho_ring = acc.ring_n ? acc.ring_sum / (double)acc.ring_n : NAN;
+  out->rho_min = unkey(acc.rmin_key);
+  out->rho_max = unkey(acc.rmax_key);
+  if (acc.nb >= 1) {
+    const double nb = (double)acc.nb;
+    out->cx = (double)acc.sx / nb;
+    out->cy = (double)acc.sy / nb;
+  }
+  if (acc.nb >= 2) {
+    // Eq. (gyr): T = <r r> - <r><r>, from exact integer sums
+    const double nb = (double)acc.nb;
+    const double txx = (double)acc.sxx / nb - out->cx * out->cx;
+    const double txy = (double)acc.sxy / nb - out->cx * out->cy;
+    const double tyy = (double)acc.syy / nb - out->cy * out->cy;
+    const double mean = 0.5 * (txx + tyy);
+    const double rad = std::sqrt(0.25 * (txx - tyy) * (txx - tyy) + txy * txy);
+    const double lM = mean + rad, lm = mean - rad;
+    out->a = 2.0 * std::sqrt(lM > 0 ? lM : 0.0);
+    out->b = 2.0 * std::sqrt(lm > 0 ? lm : 0.0);
+    out->D = (out->a + out->b) > 0 ? (out->a - out->b) / (out->a + out->b) : 0.0;
+    out->theta = 0.5 * std::atan2(2.0 * txy, txx - tyy);  // major-axis angle to x
+  }
+  return lbm_sync(h);
+}
+
+int lbm_histogram(lbm_handle* h, int32_t nbins, double lo, double hi, int64_t* counts) {
+  if (!h || !counts || nbins < 1 || nbins > 65536 || !(hi > lo)) return LBM_ERR_INVALID_ARG;
+  unsigned long long* d = nullptr;
+  const size_t b = sizeof(unsigned long long) * nbins;
+  if (cudaMalloc(&d, b) != cudaSuccess) return set_err(h, LBM_ERR_OOM);
+  int r = LBM_OK;
+  if (cuda_check(h, cudaMemsetAsync(d, 0, b, h->stream)) ||
+      cuda_check(h, launch_hist(h->aux, h->f[h->cur], nbins, lo, hi, d, h->stream)) ||
+      cuda_check(h, cudaMemcpyAsync(counts, d, b, cudaMemcpyDeviceToHost, h->stream)) ||
+      cuda_check(h, cudaStreamSynchronize(h->stream)))
+    r = h->sticky;
+  cudaFree(d);
+  if (r) return r;
+  return lbm_sync(h);
+}
+
+int lbm_sync(lbm_handle* h) {
+  if (!h) return LBM_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) set_err(h, LBM_ERR_CUDA);
+  check_device_error(h);
+  const int r = h->sticky;
+  h->sticky = LBM_OK;
+  if (r == LBM_ERR_NONFINITE) cudaMemsetAsync(h->d_err, 0, sizeof(unsigned int), h->stream);
+  return r;
+}
+
+int64_t lbm_step_count(const lbm_handle* h) { return h ? h->steps : -1; }
+
+const char* lbm_strerror(int code) {
+  switch (code) {
+    case LBM_OK: return "success";
+    case LBM_ERR_INVALID_ARG: return "invalid argument";
+    case LBM_ERR_CFL: return "CFL condition violated: max |xi| dt > ds";
+    case LBM_ERR_DENSITY_RANGE: return "density outside (0, 1/b)";
+    case LBM_ERR_UNSUPPORTED: return "unsupported option";
+    case LBM_ERR_OOM: return "device allocation failed";
+    case LBM_ERR_CUDA: return "CUDA runtime error";
+    case LBM_ERR_NONFINITE: return "non-finite or non-positive density after a step";
+    case LBM_ERR_DEVICE_BOUNDS: return "device index check failed";
+    case LBM_ERR_TIMEOUT: return "bounded device wait timed out";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

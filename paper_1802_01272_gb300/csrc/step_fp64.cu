@@ -1,0 +1,41 @@
+// step_fp64.cu -- instantiations of the fused CTU step kernel for double storage.
+#include "lbm_internal.h"
+
+namespace ctulbm {
+
+namespace {
+template <int ORDER, int LIM, bool VEC>
+void* kernel_ptr() {
+  return reinterpret_cast<void*>(&step_kernel<double, ORDER, LIM, VEC>);
+}
+
+void* select(int order, int lim, bool vec) {
+  if (order == 1) return vec ? kernel_ptr<1, 0, true>() : kernel_ptr<1, 0, false>();
+  switch (lim) {
+    case 1: return vec ? kernel_ptr<2, 1, true>() : kernel_ptr<2, 1, false>();
+    case 2: return vec ? kernel_ptr<2, 2, true>() : kernel_ptr<2, 2, false>();
+    default: return vec ? kernel_ptr<2, 0, true>() : kernel_ptr<2, 0, false>();
+  }
+}
+}  // namespace
+
+cudaError_t launch_step_f64(const StepArgs<double>& a, int order, int lim, bool vec, int grid,
+                            size_t smem, cudaStream_t s) {
+  void* fn = select(order, lim, vec);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {const_cast<StepArgs<double>*>(&a)};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(NT), args, smem, s);
+}
+
+int step_occupancy_f64(int order, int lim, bool vec, size_t smem) {
+  void* fn = select(order, lim, vec);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, NT, smem) != cudaSuccess) return 0;
+  return n;
+}
+
+}  // namespace ctulbm

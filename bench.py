@@ -33,6 +33,9 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     "sheared-bubble-6144": dict(L=6144, T=0.8, tau=1e-2, rho_ext=1.90, rho_v=0.23967, R=26.0,
                                 W=4.0, shear_dt=5e-6, walls=True, precision="fp32"),
+    # the same physics on a 2048^2 lattice (2 x 268 MB), small enough for ncu captures
+    "sheared-bubble-2048": dict(L=2048, T=0.8, tau=1e-2, rho_ext=1.90, rho_v=0.23967, R=26.0,
+                                W=4.0, shear_dt=5e-6, walls=True, precision="fp32"),
     "quiescent-bubble-4096": dict(L=4096, T=0.9, tau=1e-3, rho_ext=1.58, rho_v=0.425742, R=20.0,
                                   W=4.0, shear_dt=0.0, walls=False, precision="fp32",
                                   reservoir=True),

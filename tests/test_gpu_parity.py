@@ -152,7 +152,7 @@ def test_diagnostics_match_oracle(P, oracle_mod):
         d = L.diagnostics(threshold=(1.9 + 0.24) / 2, r_ring=50.0)
         h = L.histogram(256, 0.0, 3.0)
     o = O.diagnostics(op, f, (1.9 + 0.24) / 2, 50.0)
-    assert abs(d["mass"] - o["mass"]) / o["mass"] < 1e-13
+    assert abs(d["mass"] - o["mass"]) / o["mass"] < 1e-12   # 22400-term sums, two orders
     for n in ("nb", "sx", "sy", "sxx", "sxy", "syy"):
         assert d[n] == int(o[n])
     for n in ("rho_center", "rho_ring", "rho_min", "rho_max"):

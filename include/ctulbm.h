@@ -144,6 +144,34 @@ int lbm_diagnostics(lbm_handle* h, double threshold, double r_ring, lbm_diag* ou
  * 1 <= nbins <= 65536; synchronises the stream. */
 int lbm_histogram(lbm_handle* h, int32_t nbins, double lo, double hi, int64_t* counts);
 
+/* ---- allocation-free histogram (the paper has no counterpart) ----------------
+ * Same counts as lbm_histogram, for distributions the caller holds in device
+ * memory, without allocating anything.  It exists for callers that cannot
+ * call cudaMalloc or any allocating routine: code that runs while a stream is
+ * captured into a CUDA graph, services whose device memory is owned by
+ * another allocator or fully budgeted in advance, and callers that keep f in
+ * their own buffers with no lbm_handle.  (lbm_histogram allocates a device
+ * counts buffer on every call.)
+ *   f_device : device pointer, [16][Ly][Lx], FP64 f when precision is LBM_FP64,
+ *              float (f - w_k rho_ref) when it is LBM_FP32_SHIFTED
+ *   nbins    : 1 .. LBM_NOALLOC_MAX_BINS; more returns LBM_ERR_INVALID_ARG
+ *   counts   : host array of nbins int64, filled before return (the call
+ *              synchronises cuda_stream); bins as in lbm_histogram
+ * The bins are counted in one fixed device array of LBM_NOALLOC_MAX_BINS x 8
+ * bytes, declared at file scope in the library: every device that loads the
+ * library holds it until the process exits.  Each call zeroes the bins it
+ * uses before counting; the array keeps the last call's counts afterwards.
+ * All calls share that array, so calls that overlap on the GPU (different
+ * streams or threads) race: issue them one after another.  The first call on
+ * a device looks up the array's device address (once per device, with that
+ * device current); make that first call before any stream capture begins.
+ * Returns LBM_ERR_INVALID_ARG for bad arguments, LBM_ERR_CUDA if a CUDA call
+ * fails. */
+#define LBM_NOALLOC_MAX_BINS 4096
+int lbm_histogram_noalloc(const void* f_device, int32_t Lx, int32_t Ly, int32_t precision,
+                          double rho_ref, int32_t nbins, double lo, double hi, void* cuda_stream,
+                          int64_t* counts);
+
 /* Wait for the handle's stream and return (then clear) its sticky error. */
 int lbm_sync(lbm_handle* h);
 

@@ -89,6 +89,8 @@ def lib():
         L.lbm_sync.argtypes = [H]
         L.lbm_step_count.argtypes = [H]
         L.lbm_step_count.restype = i64
+        L.lbm_histogram_noalloc.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double,
+                                            C.c_int32, C.c_double, C.c_double, vp, P(C.c_int64)]
         L.lbm_strerror.argtypes = [C.c_int]
         L.lbm_strerror.restype = C.c_char_p
         _lib = L
@@ -164,6 +166,27 @@ def lbm_create(params: Params, stream=None):
 
 def lbm_destroy(h):
     lib().lbm_destroy(h)
+
+
+NOALLOC_MAX_BINS = 4096
+
+
+def histogram_noalloc(f, precision: int, rho_ref: float, nbins: int, lo: float, hi: float,
+                      stream=None) -> np.ndarray:
+    """lbm_histogram_noalloc on a caller-owned torch CUDA tensor f of shape
+    [16, Ly, Lx] (float64 for LBM_FP64, float32 shifted for LBM_FP32_SHIFTED).
+    Allocates no device memory; see include/ctulbm.h for the shared-array rules."""
+    import torch
+    want = torch.float64 if precision == LBM_FP64 else torch.float32
+    if not (isinstance(f, torch.Tensor) and f.is_cuda and f.dtype == want and f.is_contiguous()
+            and f.dim() == 3 and f.shape[0] == 16):
+        raise ValueError(f"expected a contiguous {want} CUDA tensor of shape [16, Ly, Lx]")
+    counts = np.zeros(nbins, dtype=np.int64)
+    _check(lib().lbm_histogram_noalloc(C.c_void_p(f.data_ptr()), f.shape[2], f.shape[1],
+                                       precision, rho_ref, nbins, lo, hi, _stream_ptr(stream),
+                                       counts.ctypes.data_as(C.POINTER(C.c_int64))),
+           "lbm_histogram_noalloc")
+    return counts
 
 
 class Lattice:

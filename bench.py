@@ -199,6 +199,8 @@ def main():
     ap.add_argument("--workload", default="sheared-bubble-6144", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ctu-order", type=int, default=None, help="override the scheme (profiling)")
+    ap.add_argument("--limiter", type=int, default=None, help="override the limiter (profiling)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
 
@@ -221,6 +223,10 @@ def main():
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
     p = lib_params(P, w)
+    if args.ctu_order is not None:
+        p.ctu_order = args.ctu_order
+    if args.limiter is not None:
+        p.limiter = args.limiter
     rho, ux, uy = initial_fields(w, p.Lx, p.Ly)
     nodes = p.Lx * p.Ly
     elem = 4 if p.precision == P.LBM_FP32_SHIFTED else 8
@@ -309,7 +315,9 @@ def main():
             "dtype": "f32" if elem == 4 else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "lattice": [p.Lx, p.Ly],
                        "storage": "fp32 shifted (f - w rho_ref)" if elem == 4 else "fp64",
-                       "scheme": "CTU2 + MC limiter", "T": p.T, "tau": p.tau,
+                       "scheme": {1: "CTU1", 2: "CTU2"}[p.ctu_order] +
+                                 {0: " + MC limiter", 1: " (Psi = 0)", 2: " (Psi = 1)"}[p.limiter]
+                                 if p.ctu_order == 2 else "CTU1", "T": p.T, "tau": p.tau,
                        "boundary": "shear walls" if w["walls"] else "periodic",
                        "l2": "inputs 2x%.2f GiB > L2, no flush" % (16 * elem * nodes / 2**30),
                        "parallelism": f"replicas x{world}"},

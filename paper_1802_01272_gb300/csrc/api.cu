@@ -112,6 +112,18 @@ void fill_step_args(lbm_handle* h, StepArgs<T>& a) {
   a.cxc = (T)(p.Lx / 2.0);
   a.cyc = (T)(p.Ly / 2.0);
   a.err = h->d_err;
+  a.xlo = (T)std::sqrt(3.0 - std::sqrt(6.0));
+  a.xhi = (T)std::sqrt(3.0 + std::sqrt(6.0));
+  for (int grp = 0; grp < 4; ++grp) {
+    const int k = 4 * grp;
+    const double x2 = h->xi[k][0] * h->xi[k][0] + h->xi[k][1] * h->xi[k][1];
+    const double Ak = (p.T - 1.0) * (x2 - 2.0) / 2.0, Bk = (p.T - 1.0) * (x2 - 4.0) / 2.0;
+    a.cls[grp].omA = (T)(om * Ak);
+    a.cls[grp].Ak = (T)Ak;
+    a.cls[grp].omB = (T)(om * Bk);
+    a.cls[grp].Bk = (T)Bk;
+    a.cls[grp].w = (T)h->w[k];
+  }
   double gb[16], gt[16];
   const double uw = p.shear_rate * p.Ly * p.ds / 2.0;
   feq_host(p, h->xi, h->w, p.rho_ext, -uw, 0.0, gb);

@@ -10,75 +10,79 @@ namespace {
 
 constexpr int BS = 256;
 
-__device__ __forceinline__ double load_f(const void* f, int storage64, long long idx) {
-  return storage64 ? static_cast<const double*>(f)[idx]
-                   : (double)static_cast<const float*>(f)[idx];
-}
-
-__device__ __forceinline__ void store_f(void* f, int storage64, long long idx, double v) {
-  if (storage64)
-    static_cast<double*>(f)[idx] = v;
-  else
-    static_cast<float*>(f)[idx] = (float)v;
-}
-
-// Eq. (herfeq) with the storage shift w_k rho_ref removed.
-__device__ void feq_shifted(const AuxArgs& a, double rho, double ux, double uy, double* out) {
-  const double T = a.Tt, u2 = ux * ux + uy * uy;
-  for (int k = 0; k < 16; ++k) {
-    const double xx = a.xi[k][0], xy = a.xi[k][1];
-    const double cu = xx * ux + xy * uy, x2 = xx * xx + xy * xy;
-    const double p = 1.0 + cu + 0.5 * (cu * cu - u2 + (T - 1.0) * (x2 - 2.0)) +
-                     cu / 6.0 * (cu * cu - 3.0 * u2 + 3.0 * (T - 1.0) * (x2 - 4.0));
-    out[k] = a.w[k] * (rho * p - a.rho_ref);
+// Velocity table in the storage precision, loaded once per thread.
+template <typename T>
+struct Vel {
+  T x[16], y[16], w[16];
+  __device__ explicit Vel(const AuxArgs& a) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      x[k] = (T)a.xi[k][0];
+      y[k] = (T)a.xi[k][1];
+      w[k] = (T)a.w[k];
+    }
   }
-}
+};
 
-__global__ void init_feq_kernel(const AuxArgs a, void* f, const double* rho, const double* ux,
+// Eq. (herfeq) with the storage shift w_k rho_ref removed:
+// f^eq - w rho_ref = w [ (rho - rho_ref) + rho (P_k - 1) ],
+// P_k - 1 = xi.u + [(xi.u)^2 - u^2 + (T-1)(xi^2-2)]/2 + xi.u [(xi.u)^2 - 3u^2 + 3(T-1)(xi^2-4)]/6
+template <typename T>
+__global__ void init_feq_kernel(const AuxArgs a, T* f, const double* rho, const double* ux,
                                 const double* uy) {
-  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= a.plane) return;
-  double fe[16];
-  feq_shifted(a, rho[q], ux[q], uy[q], fe);
-  for (int k = 0; k < 16; ++k) store_f(f, a.storage64, k * a.plane + q, fe[k]);
-}
-
-__global__ void set_f_kernel(const AuxArgs a, void* f, const double* src) {
-  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= a.plane) return;
-  for (int k = 0; k < 16; ++k)
-    store_f(f, a.storage64, k * a.plane + q, src[k * a.plane + q] - a.w[k] * a.rho_ref);
-}
-
-__global__ void get_f_kernel(const AuxArgs a, const void* f, double* dst) {
-  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= a.plane) return;
-  for (int k = 0; k < 16; ++k)
-    dst[k * a.plane + q] = load_f(f, a.storage64, k * a.plane + q) + a.w[k] * a.rho_ref;
-}
-
-__device__ __forceinline__ void node_moments(const AuxArgs& a, const void* f, long long q,
-                                             double& rho, double& mx, double& my) {
-  double d = 0.0;
-  mx = my = 0.0;
+  const Vel<T> v(a);
+  const T r = (T)rho[q], drho = (T)(rho[q] - a.rho_ref), u = (T)ux[q], w = (T)uy[q];
+  const T Tm1 = (T)(a.Tt - 1.0), u2 = u * u + w * w;
+#pragma unroll
   for (int k = 0; k < 16; ++k) {
-    const double v = load_f(f, a.storage64, k * a.plane + q);
-    d += v;
-    mx += v * a.xi[k][0];
-    my += v * a.xi[k][1];
+    const T cu = v.x[k] * u + v.y[k] * w, x2 = v.x[k] * v.x[k] + v.y[k] * v.y[k];
+    const T pm1 = cu + T(0.5) * (cu * cu - u2 + Tm1 * (x2 - T(2))) +
+                  cu / T(6) * (cu * cu - T(3) * u2 + T(3) * Tm1 * (x2 - T(4)));
+    f[k * a.plane + q] = v.w[k] * (drho + r * pm1);
   }
-  rho = a.rho_ref + d;  // sum_k w_k = 1 and sum_k w_k xi_k = 0 undo the shift
 }
 
-__global__ void moments_kernel(const AuxArgs a, const void* f, double* rho, double* ux,
-                               double* uy) {
-  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+template <typename T>
+__global__ void set_f_kernel(const AuxArgs a, T* f, const double* src) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= a.plane) return;
-  double r, mx, my;
-  node_moments(a, f, q, r, mx, my);
-  rho[q] = r;
-  ux[q] = mx / r;
-  uy[q] = my / r;
+  for (int k = 0; k < 16; ++k) f[k * a.plane + q] = (T)(src[k * a.plane + q] - a.w[k] * a.rho_ref);
+}
+
+template <typename T>
+__global__ void get_f_kernel(const AuxArgs a, const T* f, double* dst) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= a.plane) return;
+  for (int k = 0; k < 16; ++k) dst[k * a.plane + q] = (double)f[k * a.plane + q] + a.w[k] * a.rho_ref;
+}
+
+// rho - rho_ref = sum_k f_k and rho u = sum_k f_k xi_k of the stored (shifted) f
+template <typename T>
+__device__ __forceinline__ void node_moments(const AuxArgs& a, const Vel<T>& v, const T* f,
+                                             long long q, T& drho, T& mx, T& my) {
+  drho = mx = my = T(0);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const T fv = f[k * a.plane + q];
+    drho += fv;
+    mx += fv * v.x[k];
+    my += fv * v.y[k];
+  }
+}
+
+template <typename T>
+__global__ void moments_kernel(const AuxArgs a, const T* f, double* rho, double* ux, double* uy) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= a.plane) return;
+  const Vel<T> v(a);
+  T d, mx, my;
+  node_moments(a, v, f, q, d, mx, my);
+  const T r = (T)a.rho_ref + d;
+  rho[q] = (double)r;
+  ux[q] = (double)(mx / r);
+  uy[q] = (double)(my / r);
 }
 
 // order-preserving 64-bit key of a double
@@ -93,17 +97,22 @@ __device__ __forceinline__ V warp_sum(V v) {
   return v;
 }
 
-__global__ void diag_kernel(const AuxArgs a, const void* f, double thr, double r_ring,
-                            DiagAcc* acc) {
+// Ring membership |dist - r_ring| < 1/2 tested exactly on integers:
+// (2r-1)^2 < (2i - Lx)^2 + (2j - Ly)^2 < (2r+1)^2.
+template <typename T>
+__global__ void diag_kernel(const AuxArgs a, const T* f, double thr, double r_ring, DiagAcc* acc) {
+  const Vel<T> v(a);
   double mass = 0.0, ring = 0.0;
   unsigned long long nring = 0, nb = 0, sx = 0, sy = 0, sxx = 0, sxy = 0, syy = 0;
   unsigned long long kmin = ~0ULL, kmax = 0ULL;
-  const double cx = a.Lx / 2.0, cy = a.Ly / 2.0;
+  const double rin = fmax(2.0 * r_ring - 1.0, 0.0), rout = 2.0 * r_ring + 1.0;
+  const double rin2 = 2.0 * r_ring - 1.0 > 0.0 ? rin * rin : -1.0, rout2 = rout * rout;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < a.plane;
        q += (long long)gridDim.x * blockDim.x) {
-    double rho, mx, my;
-    node_moments(a, f, q, rho, mx, my);
-    const unsigned long long i = (unsigned long long)(q % a.Lx), j = (unsigned long long)(q / a.Lx);
+    T d, mx, my;
+    node_moments(a, v, f, q, d, mx, my);
+    const double rho = a.rho_ref + (double)d;
+    const long long i = q % a.Lx, j = q / a.Lx;
     mass += rho;
     const unsigned long long key = dkey(rho);
     kmin = min(kmin, key);
@@ -116,12 +125,13 @@ __global__ void diag_kernel(const AuxArgs a, const void* f, double thr, double r
       sxy += i * j;
       syy += j * j;
     }
-    const double dr = hypot((double)i - cx, (double)j - cy) - r_ring;
-    if (fabs(dr) < 0.5) {
+    const long long di = 2 * i - a.Lx, dj = 2 * j - a.Ly;
+    const double d2 = (double)(di * di + dj * dj);
+    if (d2 > rin2 && d2 < rout2) {
       ring += rho;
       nring += 1;
     }
-    if ((long long)i == a.Lx / 2 && (long long)j == a.Ly / 2) acc->rho_center = rho;
+    if (i == a.Lx / 2 && j == a.Ly / 2) acc->rho_center = rho;
   }
   mass = warp_sum(mass);
   ring = warp_sum(ring);
@@ -151,17 +161,20 @@ __global__ void diag_kernel(const AuxArgs a, const void* f, double thr, double r
   }
 }
 
-__global__ void hist_kernel(const AuxArgs a, const void* f, int nbins, double lo, double hi,
+template <typename T>
+__global__ void hist_kernel(const AuxArgs a, const T* f, int nbins, double lo, double hi,
                             unsigned long long* counts) {
   extern __shared__ unsigned int sh[];
+  const Vel<T> v(a);
   const bool priv = nbins <= 8192;
   if (priv)
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) sh[b] = 0;
   __syncthreads();
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < a.plane;
        q += (long long)gridDim.x * blockDim.x) {
-    double rho, mx, my;
-    node_moments(a, f, q, rho, mx, my);
+    T d, mx, my;
+    node_moments(a, v, f, q, d, mx, my);
+    const double rho = a.rho_ref + (double)d;
     const double t = (rho - lo) / (hi - lo) * nbins;
     if (t >= 0.0 && t < (double)nbins) {
       const int b = (int)t;
@@ -183,23 +196,37 @@ unsigned grid_for(long long n) { return (unsigned)((n + BS - 1) / BS); }
 
 cudaError_t launch_init_feq(const AuxArgs& a, void* f, const double* rho, const double* ux,
                             const double* uy, cudaStream_t s) {
-  init_feq_kernel<<<grid_for(a.plane), BS, 0, s>>>(a, f, rho, ux, uy);
+  if (a.storage64)
+    init_feq_kernel<double><<<grid_for(a.plane), BS, 0, s>>>(a, static_cast<double*>(f), rho, ux, uy);
+  else
+    init_feq_kernel<float><<<grid_for(a.plane), BS, 0, s>>>(a, static_cast<float*>(f), rho, ux, uy);
   return cudaGetLastError();
 }
 
 cudaError_t launch_set_f(const AuxArgs& a, void* f, const double* src, cudaStream_t s) {
-  set_f_kernel<<<grid_for(a.plane), BS, 0, s>>>(a, f, src);
+  if (a.storage64)
+    set_f_kernel<double><<<grid_for(a.plane), BS, 0, s>>>(a, static_cast<double*>(f), src);
+  else
+    set_f_kernel<float><<<grid_for(a.plane), BS, 0, s>>>(a, static_cast<float*>(f), src);
   return cudaGetLastError();
 }
 
 cudaError_t launch_get_f(const AuxArgs& a, const void* f, double* dst, cudaStream_t s) {
-  get_f_kernel<<<grid_for(a.plane), BS, 0, s>>>(a, f, dst);
+  if (a.storage64)
+    get_f_kernel<double><<<grid_for(a.plane), BS, 0, s>>>(a, static_cast<const double*>(f), dst);
+  else
+    get_f_kernel<float><<<grid_for(a.plane), BS, 0, s>>>(a, static_cast<const float*>(f), dst);
   return cudaGetLastError();
 }
 
 cudaError_t launch_moments(const AuxArgs& a, const void* f, double* rho, double* ux, double* uy,
                            cudaStream_t s) {
-  moments_kernel<<<grid_for(a.plane), BS, 0, s>>>(a, f, rho, ux, uy);
+  if (a.storage64)
+    moments_kernel<double><<<grid_for(a.plane), BS, 0, s>>>(a, static_cast<const double*>(f), rho,
+                                                             ux, uy);
+  else
+    moments_kernel<float><<<grid_for(a.plane), BS, 0, s>>>(a, static_cast<const float*>(f), rho,
+                                                            ux, uy);
   return cudaGetLastError();
 }
 
@@ -207,7 +234,10 @@ cudaError_t launch_diag(const AuxArgs& a, const void* f, double thr, double r_ri
                         cudaStream_t s) {
   unsigned g = grid_for(a.plane);
   if (g > 4096) g = 4096;
-  diag_kernel<<<g, BS, 0, s>>>(a, f, thr, r_ring, acc);
+  if (a.storage64)
+    diag_kernel<double><<<g, BS, 0, s>>>(a, static_cast<const double*>(f), thr, r_ring, acc);
+  else
+    diag_kernel<float><<<g, BS, 0, s>>>(a, static_cast<const float*>(f), thr, r_ring, acc);
   return cudaGetLastError();
 }
 
@@ -216,13 +246,16 @@ cudaError_t launch_hist(const AuxArgs& a, const void* f, int nbins, double lo, d
   unsigned g = grid_for(a.plane);
   if (g > 2048) g = 2048;
   const size_t sh = nbins <= 8192 ? sizeof(unsigned int) * nbins : 0;
-  hist_kernel<<<g, BS, sh, s>>>(a, f, nbins, lo, hi, counts);
+  if (a.storage64)
+    hist_kernel<double><<<g, BS, sh, s>>>(a, static_cast<const double*>(f), nbins, lo, hi, counts);
+  else
+    hist_kernel<float><<<g, BS, sh, s>>>(a, static_cast<const float*>(f), nbins, lo, hi, counts);
   return cudaGetLastError();
 }
 
 size_t step_smem_bytes(size_t elem) {
-  return elem * ((size_t)FR * 16 * SREG + 6 * (size_t)MR * REG + (size_t)NODE_W * REG +
-                 (size_t)REG_W * REG);
+  const size_t elems = (size_t)SROWS * 16 * SCOL + (size_t)FROWS * 16 * REG + 6 * (size_t)MROWS * REG;
+  return elem * elems + sizeof(int) * SG;
 }
 
 }  // namespace ctulbm

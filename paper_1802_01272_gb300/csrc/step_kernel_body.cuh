@@ -1,0 +1,345 @@
+// step_kernel_body.cuh -- the fused CTU step kernel (included by lbm_kernels.cuh
+// inside namespace ctulbm).  See the layout notes at the top of lbm_kernels.cuh.
+
+// ------------------------------------------------------------ async copies
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ int mod_pos(int a, int n) {  // a mod n for a > -n*1024
+  return (a + n * 1024) % n;
+}
+
+// Shared-memory layout (elements of T, then ints).
+template <typename T>
+struct Smem {
+  T* stage;   // [SROWS][16][SCOL] f^n rows of the strip, one group of halo per side
+  T* fs;      // [FROWS][16][REG] advected f*
+  T* rho;     // [MROWS][REG]
+  T* drho;    // rho* - rho_ref
+  T* ux;
+  T* uy;
+  T* phi;     // p^i - p^w
+  T* lap;     // 9-point Laplacian of rho*
+  int* col;   // [SG] wrapped global column of each staging group
+  __device__ Smem(unsigned char* raw) {
+    T* p = reinterpret_cast<T*>(raw);
+    stage = p;
+    p += SROWS * 16 * SCOL;
+    fs = p;
+    p += FROWS * 16 * REG;
+    rho = p;
+    drho = rho + MROWS * REG;
+    ux = drho + MROWS * REG;
+    uy = ux + MROWS * REG;
+    phi = uy + MROWS * REG;
+    lap = phi + MROWS * REG;
+    col = reinterpret_cast<int*>(lap + MROWS * REG);
+  }
+};
+
+template <typename T>
+constexpr size_t step_smem_elems() {
+  return (size_t)SROWS * 16 * SCOL + (size_t)FROWS * 16 * REG + 6 * (size_t)MROWS * REG;
+}
+
+// Stage rows [r_begin, r_end) of f^n for all 16 planes into the staging ring
+// (asynchronously when VEC).  Rows outside the lattice are wall ghost rows
+// (constant per plane) or wrap periodically.
+template <typename T, bool VEC>
+__device__ __forceinline__ void stage_rows(const StepArgs<T>& P, const Smem<T>& S, int r_begin,
+                                           int r_end, int strip) {
+  constexpr int CH = SCOL * (int)sizeof(T) / 16;  // 16-byte chunks per plane row
+  constexpr int EPC = 16 / (int)sizeof(T);         // elements per chunk
+  const int nrows = r_end - r_begin;
+  const int total = nrows * 16 * CH;
+  for (int ci = threadIdx.x; ci < total; ci += NT) {
+    const int rr = ci / (16 * CH);
+    const int rem = ci - rr * 16 * CH;
+    const int k = rem / CH;
+    const int ch = rem - k * CH;
+    const int r = r_begin + rr;
+    T* dst = S.stage + (mod_pos(r, SROWS) * 16 + k) * SCOL + ch * EPC;
+    if (P.walls && (r < 0 || r >= P.Ly)) {
+      const T gv = r < 0 ? P.v[k].gbot : P.v[k].gtop;
+#pragma unroll
+      for (int e = 0; e < EPC; ++e) dst[e] = gv;
+      continue;
+    }
+    const int rw = r < 0 ? r + P.Ly * ((-r + P.Ly - 1) / P.Ly) : (r >= P.Ly ? r % P.Ly : r);
+    const T* src_row = P.fin + (long long)k * P.plane + (long long)rw * P.Lx;
+    if (VEC) {
+      const int gg = (ch * EPC) >> 2, within = (ch * EPC) & 3;
+      cp_async16(dst, src_row + S.col[gg] + within);
+    } else {
+      const int x0 = S.col[0];  // unwrapped first staging column (scalar path)
+#pragma unroll
+      for (int e = 0; e < EPC; ++e) dst[e] = __ldg(src_row + wrapi(x0 + ch * EPC + e, P.Lx));
+    }
+  }
+}
+
+// P1 for one warp quadrant: rows a0 .. a0+RPI-1 of plane k, two rows per loop
+// trip so that the two-row history rotates by register renaming.
+template <int SX, int SY, int ORDER, int LIM, typename T>
+__device__ __forceinline__ void advect_rows(const StepArgs<T>& P, const Smem<T>& S,
+                                            AdvState<T>& st, const VelConst<T>& vc, int a0, int k,
+                                            int g) {
+  constexpr int LAG = SY > 0 ? 1 : 2;  // staged row read for output row a
+#pragma unroll 1
+  for (int j = 0; j < RPI; j += 2) {
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+      const int a = a0 + j + jj;
+      T v[12];
+      const T* srow = S.stage + (mod_pos(a + LAG, SROWS) * 16 + k) * SCOL + 4 * g;
+      sload4(srow, v);
+      sload4(srow + 4, v + 4);
+      sload4(srow + 8, v + 8);
+      T out[4];
+      advect_row<SX, SY, ORDER, LIM>(st, v, vc, out);
+      if (P.walls && (a < 0 || a >= P.Ly)) {  // ghost rows keep f^eq(rho_ext, u_wall)
+        const T gv = a < 0 ? vc.gbot : vc.gtop;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) out[i] = gv;
+      }
+      T* dst = S.fs + ((a & (FROWS - 1)) * 16 + k) * REG + 4 * g;
+      if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(dst) = make_float4(out[0], out[1], out[2], out[3]);
+      } else {
+        reinterpret_cast<double2*>(dst)[0] = make_double2(out[0], out[1]);
+        reinterpret_cast<double2*>(dst)[1] = make_double2(out[2], out[3]);
+      }
+    }
+  }
+}
+
+template <typename T, int ORDER, int LIM, bool VEC>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+    step_kernel(const __grid_constant__ StepArgs<T> P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Smem<T> S(smem_raw);
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int q = warp & 3;                          // sign quadrant of the warp
+  const int g = ((warp >> 2) << 3) | (lane & 7);   // column group 0..15
+  const int k = ((lane >> 3) << 2) | q;            // velocity of this thread in P1
+  const VelConst<T> vc = P.v[k];
+  const int Lx = P.Lx, Ly = P.Ly;
+
+  long long r0 = (long long)blockIdx.x * P.rows_per_cta;
+  const long long r1 = min(r0 + P.rows_per_cta, P.rows_total);
+
+  while (r0 < r1) {
+    const int strip = (int)(r0 / Ly);
+    const int ys = (int)(r0 % Ly);
+    const int ye = (int)min((long long)Ly, (long long)ys + (r1 - r0));
+    r0 += ye - ys;
+
+    // wrapped global columns of the staging groups (region column 0 is global
+    // column strip*TW - XOFF; the first staging column is region column -4)
+    __syncthreads();  // previous segment done with S.col and the rings
+    if (tid < SG) {
+      const int x = strip * TW - XOFF - 4 + 4 * tid;
+      S.col[tid] = VEC ? wrapi(x, Lx) : (tid == 0 ? x : 0);
+    }
+    __syncthreads();
+
+    AdvState<T> st;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) st.F0[m] = st.F1[m] = st.RY[m] = st.SY[m] = T(0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) st.A0[i] = st.A1[i] = T(0);
+
+    // P4 thread -> node mapping: a warp pair per row, 32 + 24 output columns
+    const int p4_row = warp >> 1;                           // 0..3 within the iteration
+    const int p4_col = XOFF + 32 * (warp & 1) + lane;       // region column
+    const int p4_x = strip * TW + p4_col - XOFF;            // global output column
+    const bool p4_col_ok = p4_col < XOFF + TW && p4_x < Lx;
+
+    int a0 = ys - WARMUP;
+    stage_rows<T, VEC>(P, S, a0 + 1, a0 + RPI + 2, strip);
+    cp_async_commit();
+
+    for (; a0 - 2 < ye; a0 += RPI) {
+      // ---------------- L: prefetch the rows only the next iteration needs
+      const bool more = (a0 + RPI) - 2 < ye;
+      if (more) stage_rows<T, VEC>(P, S, a0 + RPI + 2, a0 + 2 * RPI + 2, strip);
+      cp_async_commit();
+      cp_async_wait<1>();
+      __syncthreads();
+
+      // ---------------- P1: advect rows a0 .. a0+RPI-1 of plane k
+      switch (q) {
+        case 0: advect_rows<+1, +1, ORDER, LIM>(P, S, st, vc, a0, k, g); break;
+        case 1: advect_rows<-1, +1, ORDER, LIM>(P, S, st, vc, a0, k, g); break;
+        case 2: advect_rows<-1, -1, ORDER, LIM>(P, S, st, vc, a0, k, g); break;
+        default: advect_rows<+1, -1, ORDER, LIM>(P, S, st, vc, a0, k, g); break;
+      }
+      __syncthreads();
+
+      // ---------------- P2: moments of rows a0 .. a0+3, one thread per node
+      {
+        const int r = a0 + (tid >> 6), col = tid & 63;
+        const T* src = S.fs + (r & (FROWS - 1)) * 16 * REG + col;
+        T f[16];
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) f[kk] = src[kk * REG];
+        // velocity order: k = 4*group + sign, groups (lo,lo),(hi,lo),(lo,hi),(hi,hi),
+        // signs (+,+),(-,+),(-,-),(+,-)
+        T d = T(0);
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) d += f[kk];
+        const T sxa = (f[0] - f[1] - f[2] + f[3]) + (f[8] - f[9] - f[10] + f[11]);
+        const T sxb = (f[4] - f[5] - f[6] + f[7]) + (f[12] - f[13] - f[14] + f[15]);
+        const T sya = (f[0] + f[1] - f[2] - f[3]) + (f[4] + f[5] - f[6] - f[7]);
+        const T syb = (f[8] + f[9] - f[10] - f[11]) + (f[12] + f[13] - f[14] - f[15]);
+        const T mx = P.xlo * sxa + P.xhi * sxb;
+        const T my = P.xlo * sya + P.xhi * syb;
+        const T rho = P.rho_ref + d;
+        const T ir = rcp(rho);
+        const int sl = (r & (MROWS - 1)) * REG + col;
+        S.rho[sl] = rho;
+        S.drho[sl] = d;
+        S.ux[sl] = mx * ir;
+        S.uy[sl] = my * ir;
+        // p^i - p^w = rho T - [rho T/(1 - b rho) - a rho^2]   (Eqs. eder, evdw)
+        const T rT = rho * P.Tt;
+        S.phi[sl] = rT - rT * rcp(T(1) - P.b * rho) + P.a * rho * rho;
+      }
+      __syncthreads();
+
+      // ---------------- P3: Laplacian of rho* on rows a0-1 .. a0+2
+      if (tid < (REG - 2) * RPI) {
+        const int rr = tid / (REG - 2);
+        const int col = 1 + tid - rr * (REG - 2), r = a0 - 1 + rr;
+        const T* R0 = S.rho + (r & (MROWS - 1)) * REG + col;
+        const T* Rm = S.rho + ((r - 1) & (MROWS - 1)) * REG + col;
+        const T* Rp = S.rho + ((r + 1) & (MROWS - 1)) * REG + col;
+        const T nn = R0[-1] + R0[1] + Rm[0] + Rp[0];
+        const T dg = Rm[-1] + Rm[1] + Rp[-1] + Rp[1];
+        S.lap[(r & (MROWS - 1)) * REG + col] =
+            (T(2) / T(3) * nn + dg / T(6) - T(10) / T(3) * R0[0]) * P.inv_ds2;
+      }
+      __syncthreads();
+
+      // ---------------- P4: g, collision of all planes, store (rows a0-2 .. a0+1)
+      {
+        const int c = a0 - 2 + p4_row;
+        if (p4_col_ok && c >= ys && c < ye) {
+          const int col = p4_col;
+          const int sc = (c & (MROWS - 1)) * REG + col;
+          const int sm = ((c - 1) & (MROWS - 1)) * REG + col;
+          const int sp = ((c + 1) & (MROWS - 1)) * REG + col;
+          const T* ph = S.phi;
+          const T* lp = S.lap;
+          // isotropic gradient: [ (q(+1,0)-q(-1,0))/3 + (diagonal differences)/12 ] / ds
+          const T px = (ph[sc + 1] - ph[sc - 1]) * T(1.0 / 3.0) +
+                       (ph[sp + 1] - ph[sp - 1] + ph[sm + 1] - ph[sm - 1]) * T(1.0 / 12.0);
+          const T py = (ph[sp] - ph[sm]) * T(1.0 / 3.0) +
+                       (ph[sp + 1] - ph[sm + 1] + ph[sp - 1] - ph[sm - 1]) * T(1.0 / 12.0);
+          const T lx = (lp[sc + 1] - lp[sc - 1]) * T(1.0 / 3.0) +
+                       (lp[sp + 1] - lp[sp - 1] + lp[sm + 1] - lp[sm - 1]) * T(1.0 / 12.0);
+          const T ly = (lp[sp] - lp[sm]) * T(1.0 / 3.0) +
+                       (lp[sp + 1] - lp[sm + 1] + lp[sp - 1] - lp[sm - 1]) * T(1.0 / 12.0);
+          const T rho = S.rho[sc], ux = S.ux[sc], uy = S.uy[sc], drho = S.drho[sc];
+          const T ir = rcp(rho);
+          const T gdx = P.dt * P.inv_ds * (px * ir + P.kappa * lx);
+          const T gdy = P.dt * P.inv_ds * (py * ir + P.kappa * ly);
+          if (!(rho > T(0)) || !(rho < T(1e30))) atomicOr(P.err, 1u);
+          const T e = T(1) - T(0.5) * (ux * ux + uy * uy);
+          const T h = gdx * ux + gdy * uy;
+          const T p0 = P.omega * drho * ir + P.omega * (e - T(1)) - h;
+          const T p1 = e - P.Tt + T(1);
+          const T p2 = P.omega * e - h;
+          const T lo = P.xlo, hi = P.xhi;
+          const T mxu[2] = {lo * ux, hi * ux}, myu[2] = {lo * uy, hi * uy};
+          const T mxg[2] = {lo * gdx, hi * gdx}, myg[2] = {lo * gdy, hi * gdy};
+
+          T f[16];
+          const T* src = S.fs + (c & (FROWS - 1)) * 16 * REG + col;
+#pragma unroll
+          for (int kk = 0; kk < 16; ++kk) f[kk] = src[kk * REG];
+
+          T base[16];
+#pragma unroll
+          for (int kk = 0; kk < 16; ++kk) base[kk] = f[kk];
+          if (P.regularize) {
+            // Eq. (ereg): replace f* by f^eq + w [H2:A2/2 + H3:A3/6], A_n = sum f^neq xi^n
+            T m2xx = 0, m2xy = 0, m2yy = 0, m3xxx = 0, m3xxy = 0, m3xyy = 0, m3yyy = 0;
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) {
+              const T x = P.v[kk].xi_x, y = P.v[kk].xi_y, fv = f[kk];
+              m2xx += fv * x * x;
+              m2xy += fv * x * y;
+              m2yy += fv * y * y;
+              m3xxx += fv * x * x * x;
+              m3xxy += fv * x * x * y;
+              m3xyy += fv * x * y * y;
+              m3yyy += fv * y * y * y;
+            }
+            const T Tt = P.Tt;
+            const T A2xx = m2xx + P.rho_ref - rho * (ux * ux + Tt);
+            const T A2xy = m2xy - rho * ux * uy;
+            const T A2yy = m2yy + P.rho_ref - rho * (uy * uy + Tt);
+            const T A3xxx = m3xxx - rho * (ux * ux * ux + T(3) * Tt * ux);
+            const T A3xxy = m3xxy - rho * (ux * ux * uy + Tt * uy);
+            const T A3xyy = m3xyy - rho * (ux * uy * uy + Tt * ux);
+            const T A3yyy = m3yyy - rho * (uy * uy * uy + T(3) * Tt * uy);
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) {
+              const VelConst<T>& v = P.v[kk];
+              const ClassConst<T>& cl = P.cls[kk >> 2];
+              const T cu = v.xi_x * ux + v.xi_y * uy;
+              // f^eq - w rho_ref = w [ (rho - rho_ref) + rho (P_k - 1) ]
+              const T pm1 = (e - T(1) + cl.Ak) + cu * ((e + cl.Bk) + cu * (T(0.5) + cu / T(6)));
+              const T feqs = v.w * (drho + rho * pm1);
+              const T fneq = v.w * (v.r2xx * A2xx + v.r2xy * A2xy + v.r2yy * A2yy +
+                                    v.r3xxx * A3xxx + v.r3xxy * A3xxy + v.r3xyy * A3xyy +
+                                    v.r3yyy * A3yyy);
+              base[kk] = feqs + fneq;
+            }
+          }
+          T scale = T(1);
+          if (P.reservoir) {
+            const T dx = T(p4_x) - P.cxc, dy = T(c) - P.cyc;
+            if (dx * dx + dy * dy > P.rbc2) scale = P.rho_ext * ir;
+          }
+
+          T* dst = P.fout + (long long)c * Lx + p4_x;
+#pragma unroll
+          for (int grp = 0; grp < 4; ++grp) {
+            const ClassConst<T>& cl = P.cls[grp];
+            const int ix = grp & 1, iy = grp >> 1;  // magnitude index (0 lo, 1 hi) in x, y
+            const T P0 = p0 + cl.omA, P1 = p1 + cl.Ak, K1c = p2 + cl.omB, wr = cl.w * rho;
+#pragma unroll
+            for (int sgn = 0; sgn < 4; ++sgn) {
+              const int kk = 4 * grp + sgn;
+              const bool nx = sgn == 1 || sgn == 2, ny = sgn >= 2;
+              const T cu = (nx ? -mxu[ix] : mxu[ix]) + (ny ? -myu[iy] : myu[iy]);   // xi.u
+              const T D = (nx ? -mxg[ix] : mxg[ix]) + (ny ? -myg[iy] : myg[iy]);    // dt xi.g
+              const T K0 = D * P1 + P0;
+              const T K1 = K1c + D;
+              const T K2 = T(0.5) * D + P.om2;
+              // (omega f^eq + dt F_k - omega w rho_ref) / (w rho): a cubic in xi.u
+              const T poly = K0 + cu * (K1 + cu * (K2 + cu * P.om6));
+              T fn = P.one_m_omega * base[kk] + wr * poly;
+              if (P.reservoir) fn = scale * fn + cl.w * P.rho_ref * (scale - T(1));
+              dst[(long long)kk * P.plane] = fn;
+            }
+          }
+        }
+      }
+    }
+    cp_async_wait<0>();
+  }
+}

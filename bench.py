@@ -175,6 +175,62 @@ def cpu_baseline(w, seconds=15.0):
                       f"{dt:.1f} s"}
 
 
+def server_jobs(P, S, njobs, step_scale, seed=4, rate_hz=None):
+    """Config 5's job mix: lattices L^2, L in {256, 512, 1024, 2048}; T ~ U[0.75, 0.98];
+    shear rate from Ca ~ U[0, 0.4] (Ca = mu_L gamma_dot R / sigma with the seed
+    radius R, mu_L = rho_L T tau); a tanh vapour seed (R = 20, W = 4) in liquid at
+    rho_L(T); steps ~ U{5000..20000} x step_scale; Poisson arrivals."""
+    import numpy as np
+    import synth
+    from paper_1802_01272_gb300 import eos
+    rng = np.random.default_rng(seed)
+    jobs, t = [], 0.0
+    for i in range(njobs):
+        L = int(rng.choice([256, 512, 1024, 2048]))
+        T = float(rng.uniform(0.75, 0.98))
+        ca = float(rng.uniform(0.0, 0.4))
+        rl, rv = eos.coexistence(T)
+        sigma = eos.interface_tension(T, 1e-4)
+        tau = 1e-2
+        gdot = ca * sigma / (rl * T * tau * 20 * DS)
+        p = P.Params(Lx=L, Ly=L, T=T, tau=tau, dt=DT, ds=DS, rho_ext=rl, rho_ref=rl,
+                     boundary=P.LBM_BC_SHEAR_WALLS if gdot > 0 else P.LBM_BC_PERIODIC,
+                     shear_rate=gdot)
+        rho, ux, uy = synth.bubble(L, L, rl, rv, 20.0, 4.0)
+        if gdot > 0:
+            ux = synth.linear_shear(L, L, gdot * L * DS / 2)
+        nsteps = max(10, int(int(rng.integers(5000, 20001)) * step_scale))
+        jobs.append(S.Job(params=p, rho=rho, ux=ux, uy=uy, nsteps=nsteps, arrival=t,
+                          diag_threshold=0.5 * (rl + rv)))
+        t += float(rng.exponential(1.0 / rate_hz)) if rate_hz else 0.0
+    return jobs
+
+
+def run_server_bench(P, stream, njobs, step_scale):
+    """Continuous batching vs the same jobs one at a time (same GPU, same jobs)."""
+    from paper_1802_01272_gb300 import server as S
+    jobs = server_jobs(P, S, njobs, step_scale)
+    work = sum(j.node_updates for j in jobs)
+    # offered load ~1.2x of the serial throughput, measured on the first job
+    probe = server_jobs(P, S, 1, step_scale)[0]
+    t0 = time.perf_counter()
+    S.run_serial([probe], stream)
+    rate = probe.node_updates / (time.perf_counter() - t0)
+    mean_work = work / njobs
+    jobs = server_jobs(P, S, njobs, step_scale, rate_hz=1.2 * rate / mean_work)
+    serial_jobs = server_jobs(P, S, njobs, step_scale, rate_hz=1.2 * rate / mean_work)
+    srv = S.SweepServer(mem_budget_bytes=int(64e9), stream=stream, chunk=100)
+    for j in jobs:
+        srv.submit(j)
+    st = srv.run()
+    ss = S.run_serial(serial_jobs, stream)
+    return {"jobs": njobs, "steps_scale": step_scale, "node_updates": work,
+            "batched": {"glups": st.glups, "p50_s": st.pct(50), "p99_s": st.pct(99),
+                        "makespan_s": st.makespan},
+            "serial": {"glups": ss.glups, "p50_s": ss.pct(50), "p99_s": ss.pct(99),
+                       "makespan_s": ss.makespan}}
+
+
 def run_reference(args, w, rank, world):
     if rank != 0:
         return
@@ -199,6 +255,9 @@ def main():
     ap.add_argument("--workload", default="sheared-bubble-6144", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--server", type=int, default=0, metavar="NJOBS",
+                    help="also run the sweep-server comparison over NJOBS config-5 jobs")
+    ap.add_argument("--server-step-scale", type=float, default=0.05)
     ap.add_argument("--ctu-order", type=int, default=None, help="override the scheme (profiling)")
     ap.add_argument("--limiter", type=int, default=None, help="override the limiter (profiling)")
     args = ap.parse_args()
@@ -282,15 +341,14 @@ def main():
         hr, hx, hy = (t.numpy() for t in pin[:3])
         orho, oux, ouy = (t.numpy() for t in pin[3:])
         E = P.Lattice(p, stream)
+        thr = 0.5 * (w["rho_ext"] + w["rho_v"])
         E.init_rho_u(hr, hx, hy)
-        E.step(2)
-        E.diagnostics(threshold=0.5 * (w["rho_ext"] + w["rho_v"]))
+        E.step_diag(2, thr)
         barrier()
         t0 = time.perf_counter()
         E.init_rho_u(hr, hx, hy)
         for _ in range(args.steps):
-            E.step(1)
-            E.diagnostics(threshold=0.5 * (w["rho_ext"] + w["rho_v"]))
+            E.step_diag(1, thr)          # one step, its diagnostics record read back
         E.moments(out=(orho, oux, ouy))
         barrier()
         te = max_over_ranks(time.perf_counter() - t0)
@@ -299,9 +357,13 @@ def main():
         e2e = {"value": world * nodes * args.steps / te / 1e9, "unit": "GLUPS",
                "h2d_bytes_per_step": int(3 * 8 * nodes / args.steps),
                "d2h_bytes_per_step": int(diag_bytes + 3 * 8 * nodes / args.steps),
-               "region": "init_rho_u from pinned host + per step (lbm_step(1) + lbm_diagnostics "
-                         "record to host) + final lbm_moments to host"}
+               "region": "init_rho_u from pinned host + per step lbm_step_diag(1) (diagnostics "
+                         "record reduced in the step, read back) + final lbm_moments to host"}
     L.close()
+
+    srv = None
+    if args.server:
+        srv = run_server_bench(P, stream, args.server, args.server_step_scale)
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -331,6 +393,8 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cb,
         }
+        if srv is not None:
+            line["server"] = srv
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

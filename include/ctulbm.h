@@ -131,6 +131,27 @@ int lbm_get_f_device(lbm_handle* h, double* f);
 /* Advance n >= 0 steps on the handle's stream (asynchronous; one fused kernel per step). */
 int lbm_step(lbm_handle* h, int64_t n);
 
+/* Advance n >= 1 steps and return the diagnostics of the final state, reduced
+ * inside the last step's kernel (no extra pass over f): mass, bubble sites
+ * rho < threshold, their integer moment sums and the Eq. (gyr) shape.
+ * rho_center, rho_ring, rho_min and rho_max are NaN (use lbm_diagnostics).
+ * Synchronises the stream. */
+int lbm_step_diag(lbm_handle* h, int64_t n, double threshold, lbm_diag* out);
+
+/* Advance `count` distinct lattices n >= 0 steps together (parameter sweeps,
+ * many small jobs).  FP32-shifted lattices with Lx % 4 == 0 and the same
+ * scheme and limiter as handles[0] share one fused launch per step, up to 16
+ * per launch: their rows are split evenly over one persistent grid, which
+ * keeps the GPU full when each lattice alone would not.  Other lattices step
+ * on their own.  Every node goes through the same sequence of operations as in
+ * lbm_step; the batched kernel is compiled separately, so FP32 results agree
+ * with stepping alone to rounding (the compiler may fuse multiply-adds
+ * differently), FP64 lattices step alone and agree exactly.  All handles must share
+ * one device and one stream (handles[0]'s); asynchronous like lbm_step.
+ * Returns LBM_ERR_INVALID_ARG for a null or repeated handle or a stream
+ * mismatch. */
+int lbm_step_many(lbm_handle* const* handles, int32_t count, int64_t n);
+
 /* rho, u = (sum_k f_k, sum_k f_k xi_k / rho) of the current state, FP64 [Ly][Lx].
  * The host version synchronises the stream. */
 int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy);

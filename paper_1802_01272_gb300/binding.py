@@ -55,7 +55,8 @@ class lbm_diag(C.Structure):
 
 
 _lib = None
-EXPORTS = ["lbm_default_params", "lbm_create", "lbm_destroy", "lbm_init_rho_u",
+EXPORTS = ["lbm_default_params", "lbm_create", "lbm_destroy", "lbm_init_rho_u", "lbm_step_many",
+           "lbm_step_diag",
            "lbm_init_rho_u_device", "lbm_set_f", "lbm_get_f", "lbm_set_f_device",
            "lbm_get_f_device", "lbm_step", "lbm_moments", "lbm_moments_device",
            "lbm_diagnostics", "lbm_histogram", "lbm_sync", "lbm_step_count", "lbm_strerror"]
@@ -84,6 +85,8 @@ def lib():
         for n in ("lbm_set_f", "lbm_get_f", "lbm_set_f_device", "lbm_get_f_device"):
             getattr(L, n).argtypes = [H, vp]
         L.lbm_step.argtypes = [H, i64]
+        L.lbm_step_many.argtypes = [P(H), C.c_int32, i64]
+        L.lbm_step_diag.argtypes = [H, i64, C.c_double, P(lbm_diag)]
         L.lbm_diagnostics.argtypes = [H, C.c_double, C.c_double, P(lbm_diag)]
         L.lbm_histogram.argtypes = [H, C.c_int32, C.c_double, C.c_double, P(C.c_int64)]
         L.lbm_sync.argtypes = [H]
@@ -168,6 +171,13 @@ def lbm_destroy(h):
     lib().lbm_destroy(h)
 
 
+def step_many(lattices, n: int):
+    """lbm_step_many over Lattice objects: one fused launch per step for all
+    compatible lattices (equal to stepping each alone, to FP32 rounding)."""
+    arr = (C.c_void_p * len(lattices))(*[L.handle for L in lattices])
+    _check(lib().lbm_step_many(arr, len(lattices), int(n)), "lbm_step_many")
+
+
 NOALLOC_MAX_BINS = 4096
 
 
@@ -247,6 +257,13 @@ class Lattice:
 
     def step(self, n: int = 1):
         _check(lib().lbm_step(self._h, int(n)), "lbm_step")
+
+    def step_diag(self, n: int, threshold: float) -> dict:
+        """lbm_step_diag: n steps, diagnostics of the final state fused into the
+        last step (mass, bubble sites, gyration shape)."""
+        d = lbm_diag()
+        _check(lib().lbm_step_diag(self._h, int(n), threshold, C.byref(d)), "lbm_step_diag")
+        return {n_: getattr(d, n_) for n_, _ in lbm_diag._fields_}
 
     def moments(self, out=None):
         """(rho, ux, uy) as float64 [Ly][Lx]; `out` may supply three C-contiguous

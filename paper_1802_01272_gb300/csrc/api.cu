@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <new>
 
 #include "ctulbm.h"
@@ -23,6 +24,7 @@ struct lbm_handle {
   void* f[2] = {nullptr, nullptr};
   int cur = 0;
   unsigned int* d_err = nullptr;
+  unsigned long long* d_sched = nullptr;  // work-item counters of the step kernel
   DiagAcc* d_acc = nullptr;
   double* d_work = nullptr;       // 3 planes of FP64 for moments / init staging
   size_t work_elems = 0;
@@ -31,6 +33,7 @@ struct lbm_handle {
   int grid = 0;
   long long rows_per_cta = 0;
   int nstrip = 0;
+  int row_block = 256;
   bool vec = false;
   size_t smem = 0;
   double xi[16][2], w[16];
@@ -80,16 +83,33 @@ int cuda_check(lbm_handle* h, cudaError_t e) {
 
 double rho_ref_of(const lbm_params& p) { return p.precision == LBM_FP64 ? 0.0 : p.rho_ref; }
 
+// FP32 keeps the relaxation and the corner weights exactly balanced: omega and
+// the off-corner weights are put on the 2^-24 grid, so that 1 - omega and
+// c00 = 1 - c10 - c01 - c11 are exact in FP32.  Rounding them separately would
+// leave (1 - omega) + omega and the weight sum 2e-8 off 1, a systematic damping
+// of every deviation by that much per step (it shows as +2% in the decay rate
+// of a shear wave over 2e5 steps).  FP64 keeps the exact values.
+double snap(double v, bool fp32) {
+  return fp32 ? std::ldexp(std::nearbyint(std::ldexp(v, 24)), -24) : v;
+}
+
 template <typename T>
 void fill_step_args(lbm_handle* h, StepArgs<T>& a) {
   const lbm_params& p = h->p;
-  const double lam = p.dt / p.ds, om = p.dt / p.tau, rr = rho_ref_of(p);
+  const bool f32 = sizeof(T) == 4;
+  const double lam = p.dt / p.ds, om = snap(p.dt / p.tau, f32), rr = rho_ref_of(p);
   a.Lx = p.Lx;
   a.Ly = p.Ly;
   a.plane = (long long)p.Lx * p.Ly;
   a.nstrip = h->nstrip;
   a.rows_total = (long long)h->nstrip * p.Ly;
   a.rows_per_cta = h->rows_per_cta;
+  a.row_block = h->row_block;
+  a.items = (long long)((p.Ly + h->row_block - 1) / h->row_block) * h->nstrip;
+  a.sched = h->d_sched;
+  a.diag_mass = nullptr;
+  a.diag_sums = nullptr;
+  a.diag_thr = (T)0;
   a.walls = p.boundary == LBM_BC_SHEAR_WALLS;
   a.reservoir = p.reservoir;
   a.regularize = p.regularize;
@@ -139,10 +159,12 @@ void fill_step_args(lbm_handle* h, StepArgs<T>& a) {
     v.xi_x = (T)x;
     v.xi_y = (T)y;
     v.w = (T)h->w[k];
-    v.c00 = (T)((1.0 - cx) * (1.0 - cy));
-    v.c10 = (T)(cx * (1.0 - cy));
-    v.c01 = (T)(cy * (1.0 - cx));
-    v.c11 = (T)(cx * cy);
+    const double c10 = snap(cx * (1.0 - cy), f32), c01 = snap(cy * (1.0 - cx), f32);
+    const double c11 = snap(cx * cy, f32);
+    v.c00 = (T)(1.0 - c10 - c01 - c11);
+    v.c10 = (T)c10;
+    v.c01 = (T)c01;
+    v.c11 = (T)c11;
     // U2 = -lam hx [(1-cy) dS^x + cy dS^x(j - sgn_y)] - lam hy [(1-cx) dS^y + cx dS^y(i - sgn_x)],
     // with the kernel's half-limited jumps (hence the factor 2)
     v.a1 = (T)(2.0 * lam * hx * (1.0 - cy));
@@ -189,6 +211,48 @@ int validate(const lbm_params* p) {
   if (!std::isfinite(p->shear_rate)) return LBM_ERR_INVALID_ARG;
   if (p->precision == LBM_FP32_SHIFTED && !std::isfinite(p->rho_ref)) return LBM_ERR_INVALID_ARG;
   return LBM_OK;
+}
+
+// Host finishing of a diagnostics record: centroid and Eq. (gyr) shape from
+// the exact integer sums; probe fields only when the full reduction ran.
+void finish_diag(const DiagAcc& acc, bool full, lbm_diag* out) {
+  auto unkey = [](unsigned long long k) {
+    unsigned long long b = (k & 0x8000000000000000ULL) ? (k & ~0x8000000000000000ULL) : ~k;
+    double v;
+    std::memcpy(&v, &b, sizeof(v));
+    return v;
+  };
+  std::memset(out, 0, sizeof(*out));
+  out->mass = acc.mass;
+  out->nb = (int64_t)acc.nb;
+  out->sx = (int64_t)acc.sx;
+  out->sy = (int64_t)acc.sy;
+  out->sxx = (int64_t)acc.sxx;
+  out->sxy = (int64_t)acc.sxy;
+  out->syy = (int64_t)acc.syy;
+  out->rho_center = full ? acc.rho_center : NAN;
+  out->rho_ring = full && acc.ring_n ? acc.ring_sum / (double)acc.ring_n : NAN;
+  out->rho_min = full ? unkey(acc.rmin_key) : NAN;
+  out->rho_max = full ? unkey(acc.rmax_key) : NAN;
+  if (acc.nb >= 1) {
+    const double nb = (double)acc.nb;
+    out->cx = (double)acc.sx / nb;
+    out->cy = (double)acc.sy / nb;
+  }
+  if (acc.nb >= 2) {
+    // Eq. (gyr): T = <r r> - <r><r>, from exact integer sums
+    const double nb = (double)acc.nb;
+    const double txx = (double)acc.sxx / nb - out->cx * out->cx;
+    const double txy = (double)acc.sxy / nb - out->cx * out->cy;
+    const double tyy = (double)acc.syy / nb - out->cy * out->cy;
+    const double mean = 0.5 * (txx + tyy);
+    const double rad = std::sqrt(0.25 * (txx - tyy) * (txx - tyy) + txy * txy);
+    const double lM = mean + rad, lm = mean - rad;
+    out->a = 2.0 * std::sqrt(lM > 0 ? lM : 0.0);
+    out->b = 2.0 * std::sqrt(lm > 0 ? lm : 0.0);
+    out->D = (out->a + out->b) > 0 ? (out->a - out->b) / (out->a + out->b) : 0.0;
+    out->theta = 0.5 * std::atan2(2.0 * txy, txx - tyy);  // major-axis angle to x
+  }
 }
 
 int check_device_error(lbm_handle* h) {
@@ -251,11 +315,13 @@ int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out) {
   if ((e = cudaMalloc(&h->f[0], bytes)) != cudaSuccess ||
       (e = cudaMalloc(&h->f[1], bytes)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_err, sizeof(unsigned int))) != cudaSuccess ||
-      (e = cudaMalloc(&h->d_acc, sizeof(DiagAcc))) != cudaSuccess) {
+      (e = cudaMalloc(&h->d_acc, sizeof(DiagAcc))) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_sched, 2 * sizeof(unsigned long long))) != cudaSuccess) {
     lbm_destroy(h);
     return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
   }
   cudaMemsetAsync(h->d_err, 0, sizeof(unsigned int), h->stream);
+  cudaMemsetAsync(h->d_sched, 0, 2 * sizeof(unsigned long long), h->stream);
 
   // launch geometry: strips of TW output columns, rows split evenly over a
   // persistent grid of (SMs x resident CTAs), at least 48 rows per CTA
@@ -271,14 +337,17 @@ int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out) {
     lbm_destroy(h);
     return LBM_ERR_CUDA;
   }
+  // work items: row blocks of up to 256 rows x strips; blocks shrink (down to
+  // 96 rows, where the 5-row warm-up still costs < 8 %) when a lattice would
+  // leave the grid with fewer than ~3 items per CTA
   const long long rows_total = (long long)h->nstrip * p->Ly;
-  long long grid = (long long)nsm * occ;
-  const long long by_rows = (rows_total + 47) / 48;
-  if (grid > by_rows) grid = by_rows;
-  if (grid < 1) grid = 1;
-  h->rows_per_cta = (rows_total + grid - 1) / grid;
-  h->grid = (int)((rows_total + h->rows_per_cta - 1) / h->rows_per_cta);
-
+  const long long grid_max = (long long)nsm * occ;
+  long long rb = rows_total / (3 * grid_max);
+  rb = rb < 96 ? 96 : (rb > 256 ? 256 : rb);
+  h->row_block = (int)rb;
+  const long long items = (long long)((p->Ly + rb - 1) / rb) * h->nstrip;
+  h->grid = (int)(items < grid_max ? items : grid_max);
+  h->rows_per_cta = 0;
   if (h->elem == 4)
     fill_step_args<float>(h, h->a32);
   else
@@ -303,6 +372,7 @@ void lbm_destroy(lbm_handle* h) {
   cudaFree(h->f[1]);
   cudaFree(h->d_err);
   cudaFree(h->d_acc);
+  cudaFree(h->d_sched);
   cudaFree(h->d_work);
   delete h;
 }
@@ -412,6 +482,117 @@ int lbm_step(lbm_handle* h, int64_t n) {
   return LBM_OK;
 }
 
+int lbm_step_many(lbm_handle* const* handles, int32_t count, int64_t n) {
+  if (!handles || count < 1 || n < 0) return LBM_ERR_INVALID_ARG;
+  lbm_handle* h0 = handles[0];
+  if (!h0) return LBM_ERR_INVALID_ARG;
+  const int lim0 = h0->p.ctu_order == 1 ? 0 : h0->p.limiter;
+  for (int i = 0; i < count; ++i) {
+    lbm_handle* h = handles[i];
+    if (!h || h->stream != h0->stream || h->device != h0->device) return LBM_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == h) return LBM_ERR_INVALID_ARG;  // each lattice once
+  }
+  // Lattices that cannot share a launch (FP64 storage, another scheme or
+  // limiter, the scalar column path) step on their own, one launch per step.
+  lbm_handle* group[MAXB];
+  int ng = 0;
+  auto flush = [&](int64_t steps) -> int {
+    if (ng == 0) return LBM_OK;
+    int grid_max = 0;
+    {
+      int occ = step_batch_occupancy_f32(h0->p.ctu_order, lim0, true, group[0]->smem);
+      int nsm = 0;
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h0->device);
+      grid_max = occ * nsm;
+      if (grid_max < 1) return set_err(h0, LBM_ERR_CUDA);
+    }
+    std::unique_ptr<BatchArgs<float>> bp(new (std::nothrow) BatchArgs<float>());
+    if (!bp) return set_err(h0, LBM_ERR_OOM);
+    BatchArgs<float>& b = *bp;  // ~31 KB, copied into the launch's parameter space
+    long long total = 0;
+    b.count = ng;
+    b.sched = h0->d_sched;
+    for (int i = 0; i < ng; ++i) {
+      b.item_start[i] = total;
+      total += group[i]->a32.items;
+    }
+    b.item_start[ng] = total;
+    const int g = (int)(total < grid_max ? total : grid_max);
+    for (int64_t s = 0; s < steps; ++s) {
+      for (int i = 0; i < ng; ++i) {
+        lbm_handle* h = group[i];
+        b.L[i] = h->a32;
+        b.L[i].fin = static_cast<const float*>(h->f[h->cur]);
+        b.L[i].fout = static_cast<float*>(h->f[1 - h->cur]);
+      }
+      cudaError_t e = launch_step_batch_f32(b, h0->p.ctu_order, lim0, true, g, group[0]->smem,
+                                            h0->stream);
+      if (e != cudaSuccess) return cuda_check(h0, e);
+      for (int i = 0; i < ng; ++i) {
+        group[i]->cur ^= 1;
+        group[i]->steps += 1;
+      }
+    }
+    ng = 0;
+    return LBM_OK;
+  };
+  for (int i = 0; i < count; ++i) {
+    lbm_handle* h = handles[i];
+    const int lim = h->p.ctu_order == 1 ? 0 : h->p.limiter;
+    const bool batchable = h->elem == 4 && h->vec && h->p.ctu_order == h0->p.ctu_order &&
+                           lim == lim0;
+    if (!batchable) {
+      int r = lbm_step(h, n);
+      if (r) return r;
+      continue;
+    }
+    group[ng++] = h;
+    if (ng == MAXB) {
+      int r = flush(n);
+      if (r) return r;
+    }
+  }
+  return flush(n);
+}
+
+int lbm_step_diag(lbm_handle* h, int64_t n, double threshold, lbm_diag* out) {
+  if (!h || !out || n < 1) return LBM_ERR_INVALID_ARG;
+  int r = lbm_step(h, n - 1);
+  if (r) return r;
+  DiagAcc acc;
+  std::memset(&acc, 0, sizeof(acc));
+  if (cuda_check(h, cudaMemsetAsync(h->d_acc, 0, sizeof(DiagAcc), h->stream))) return h->sticky;
+  const int lim = h->p.ctu_order == 1 ? 0 : h->p.limiter;
+  cudaError_t e;
+  if (h->elem == 4) {
+    StepArgs<float> a = h->a32;
+    a.fin = static_cast<const float*>(h->f[h->cur]);
+    a.fout = static_cast<float*>(h->f[1 - h->cur]);
+    a.diag_mass = &h->d_acc->mass;
+    a.diag_sums = &h->d_acc->nb;
+    a.diag_thr = (float)threshold;
+    e = launch_step_f32(a, h->p.ctu_order, lim, h->vec, h->grid, h->smem, h->stream);
+  } else {
+    StepArgs<double> a = h->a64;
+    a.fin = static_cast<const double*>(h->f[h->cur]);
+    a.fout = static_cast<double*>(h->f[1 - h->cur]);
+    a.diag_mass = &h->d_acc->mass;
+    a.diag_sums = &h->d_acc->nb;
+    a.diag_thr = threshold;
+    e = launch_step_f64(a, h->p.ctu_order, lim, h->vec, h->grid, h->smem, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_check(h, e);
+  h->cur ^= 1;
+  h->steps += 1;
+  if (cuda_check(h, cudaMemcpyAsync(&acc, h->d_acc, sizeof(acc), cudaMemcpyDeviceToHost,
+                                    h->stream)) ||
+      cuda_check(h, cudaStreamSynchronize(h->stream)))
+    return h->sticky;
+  finish_diag(acc, false, out);
+  return lbm_sync(h);
+}
+
 int lbm_moments_device(lbm_handle* h, double* rho, double* ux, double* uy) {
   if (!h || !rho || !ux || !uy) return LBM_ERR_INVALID_ARG;
   return cuda_check(h, launch_moments(h->aux, h->f[h->cur], rho, ux, uy, h->stream));
@@ -446,43 +627,7 @@ int lbm_diagnostics(lbm_handle* h, double threshold, double r_ring, lbm_diag* ou
                                     h->stream)) ||
       cuda_check(h, cudaStreamSynchronize(h->stream)))
     return h->sticky;
-  auto unkey = [](unsigned long long k) {
-    unsigned long long b = (k & 0x8000000000000000ULL) ? (k & ~0x8000000000000000ULL) : ~k;
-    double v;
-    std::memcpy(&v, &b, sizeof(v));
-    return v;
-  };
-  std::memset(out, 0, sizeof(*out));
-  out->mass = acc.mass;
-  out->nb = (int64_t)acc.nb;
-  out->sx = (int64_t)acc.sx;
-  out->sy = (int64_t)acc.sy;
-  out->sxx = (int64_t)acc.sxx;
-  out->sxy = (int64_t)acc.sxy;
-  out->syy = (int64_t)acc.syy;
-  out->rho_center = acc.rho_center;
-  out->rho_ring = acc.ring_n ? acc.ring_sum / (double)acc.ring_n : NAN;
-  out->rho_min = unkey(acc.rmin_key);
-  out->rho_max = unkey(acc.rmax_key);
-  if (acc.nb >= 1) {
-    const double nb = (double)acc.nb;
-    out->cx = (double)acc.sx / nb;
-    out->cy = (double)acc.sy / nb;
-  }
-  if (acc.nb >= 2) {
-    // Eq. (gyr): T = <r r> - <r><r>, from exact integer sums
-    const double nb = (double)acc.nb;
-    const double txx = (double)acc.sxx / nb - out->cx * out->cx;
-    const double txy = (double)acc.sxy / nb - out->cx * out->cy;
-    const double tyy = (double)acc.syy / nb - out->cy * out->cy;
-    const double mean = 0.5 * (txx + tyy);
-    const double rad = std::sqrt(0.25 * (txx - tyy) * (txx - tyy) + txy * txy);
-    const double lM = mean + rad, lm = mean - rad;
-    out->a = 2.0 * std::sqrt(lM > 0 ? lM : 0.0);
-    out->b = 2.0 * std::sqrt(lm > 0 ? lm : 0.0);
-    out->D = (out->a + out->b) > 0 ? (out->a - out->b) / (out->a + out->b) : 0.0;
-    out->theta = 0.5 * std::atan2(2.0 * txy, txx - tyy);  // major-axis angle to x
-  }
+  finish_diag(acc, true, out);
   return lbm_sync(h);
 }
 

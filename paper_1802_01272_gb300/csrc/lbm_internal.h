@@ -24,6 +24,10 @@ cudaError_t launch_step_f32(const StepArgs<float>& a, int order, int lim, bool v
                             size_t smem, cudaStream_t s);
 cudaError_t launch_step_f64(const StepArgs<double>& a, int order, int lim, bool vec, int grid,
                             size_t smem, cudaStream_t s);
+// Several FP32 lattices in one launch (same scheme, limiter and column path).
+cudaError_t launch_step_batch_f32(const BatchArgs<float>& b, int order, int lim, bool vec,
+                                  int grid, size_t smem, cudaStream_t s);
+int step_batch_occupancy_f32(int order, int lim, bool vec, size_t smem);
 // Largest resident CTAs per SM for the selected step kernel (0 on error).
 int step_occupancy_f32(int order, int lim, bool vec, size_t smem);
 int step_occupancy_f64(int order, int lim, bool vec, size_t smem);

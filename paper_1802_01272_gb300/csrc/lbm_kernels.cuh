@@ -76,6 +76,14 @@ struct StepArgs {
   int nstrip;
   long long rows_total;     // nstrip * Ly
   long long rows_per_cta;
+  int row_block;            // rows per work item
+  long long items;          // work items: ceil(Ly / row_block) * nstrip, row-block major
+  unsigned long long* sched;  // [2]: next item, CTAs done (reset by the last CTA)
+  // fused diagnostics of the state after this step (null: off): FP64 mass,
+  // bubble sites rho < diag_thr and their exact integer moment sums
+  double* diag_mass;
+  unsigned long long* diag_sums;  // [6]: nb, sx, sy, sxx, sxy, syy
+  T diag_thr;
   int walls, reservoir, regularize;
   T rho_ref, Tt, a, b, kappa, inv_ds, inv_ds2, dt, omega, one_m_omega, om2, om6;
   T rho_ext, rbc2, cxc, cyc;
@@ -83,6 +91,16 @@ struct StepArgs {
   T xlo, xhi;               // |xi| components sqrt(3 - sqrt 6), sqrt(3 + sqrt 6)
   ClassConst<T> cls[4];     // groups (lo,lo), (hi,lo), (lo,hi), (hi,hi)
   VelConst<T> v[16];
+};
+
+constexpr int MAXB = 16;  // lattices per batched launch (kernel parameter space)
+
+template <typename T>
+struct BatchArgs {
+  int count;
+  unsigned long long* sched;       // [2] work counter and done counter
+  long long item_start[MAXB + 1];  // prefix sums of the lattices' work items
+  StepArgs<T> L[MAXB];
 };
 
 // ---------------------------------------------------------------- helpers

@@ -38,4 +38,40 @@ int step_occupancy_f32(int order, int lim, bool vec, size_t smem) {
   return n;
 }
 
+namespace {
+template <int ORDER, int LIM, bool VEC>
+void* batch_ptr() {
+  return reinterpret_cast<void*>(&step_batch_kernel<float, ORDER, LIM, VEC>);
+}
+void* select_batch(int order, int lim, bool vec) {
+  if (order == 1) return vec ? batch_ptr<1, 0, true>() : batch_ptr<1, 0, false>();
+  switch (lim) {
+    case 1: return vec ? batch_ptr<2, 1, true>() : batch_ptr<2, 1, false>();
+    case 2: return vec ? batch_ptr<2, 2, true>() : batch_ptr<2, 2, false>();
+    default: return vec ? batch_ptr<2, 0, true>() : batch_ptr<2, 0, false>();
+  }
+}
+}  // namespace
+
+static_assert(sizeof(BatchArgs<float>) <= 32764, "batched launch exceeds kernel parameter space");
+
+cudaError_t launch_step_batch_f32(const BatchArgs<float>& b, int order, int lim, bool vec, int grid,
+                                  size_t smem, cudaStream_t s) {
+  void* fn = select_batch(order, lim, vec);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {const_cast<BatchArgs<float>*>(&b)};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(NT), args, smem, s);
+}
+
+int step_batch_occupancy_f32(int order, int lim, bool vec, size_t smem) {
+  void* fn = select_batch(order, lim, vec);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, NT, smem) != cudaSuccess) return 0;
+  return n;
+}
+
 }  // namespace ctulbm

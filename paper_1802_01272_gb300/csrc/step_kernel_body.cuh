@@ -30,6 +30,8 @@ struct Smem {
   T* phi;     // p^i - p^w
   T* lap;     // 9-point Laplacian of rho*
   int* col;   // [SG] wrapped global column of each staging group
+  double* dmass;              // fused diagnostics: per-CTA accumulators
+  unsigned long long* dsums;  // [6]
   __device__ Smem(unsigned char* raw) {
     T* p = reinterpret_cast<T*>(raw);
     stage = p;
@@ -43,6 +45,8 @@ struct Smem {
     phi = uy + MROWS * REG;
     lap = phi + MROWS * REG;
     col = reinterpret_cast<int*>(lap + MROWS * REG);
+    dmass = reinterpret_cast<double*>(col + SG + (SG & 1));  // 8-byte aligned after 18 ints
+    dsums = reinterpret_cast<unsigned long long*>(dmass + 1);
   }
 };
 
@@ -51,38 +55,68 @@ constexpr size_t step_smem_elems() {
   return (size_t)SROWS * 16 * SCOL + (size_t)FROWS * 16 * REG + 6 * (size_t)MROWS * REG;
 }
 
+// Staging: a staged row holds 16 planes x CH 16-byte chunks.  Thread t copies
+// chunks t, t + NT, ... of every staged row, so its (plane, column) slots are
+// fixed for a whole segment and a row costs one address add per chunk.
+template <typename T>
+struct StageSlots {
+  static constexpr int CH = SCOL * (int)sizeof(T) / 16;  // 16-byte chunks per plane row
+  static constexpr int EPC = 16 / (int)sizeof(T);         // elements per chunk
+  static constexpr int PER_ROW = 16 * CH;
+  static constexpr int NS = (PER_ROW + NT - 1) / NT;      // chunks per thread per row
+  long long src[NS];  // element offset of the chunk in row 0 of f^n (plane and column)
+  int dst[NS];        // element offset inside a staged row
+  __device__ StageSlots(const StepArgs<T>& P, const Smem<T>& S, bool vec) {
+#pragma unroll
+    for (int m = 0; m < NS; ++m) {
+      const int c = threadIdx.x + NT * m;
+      const int k = c / CH, ch = c - (c / CH) * CH;
+      const int gg = (ch * EPC) >> 2, within = (ch * EPC) & 3;
+      dst[m] = k * SCOL + ch * EPC;
+      src[m] = c < PER_ROW ? (long long)k * P.plane + (vec ? S.col[gg] + within : 0) : 0;
+    }
+  }
+};
+
 // Stage rows [r_begin, r_end) of f^n for all 16 planes into the staging ring
 // (asynchronously when VEC).  Rows outside the lattice are wall ghost rows
 // (constant per plane) or wrap periodically.
 template <typename T, bool VEC>
-__device__ __forceinline__ void stage_rows(const StepArgs<T>& P, const Smem<T>& S, int r_begin,
-                                           int r_end, int strip) {
-  constexpr int CH = SCOL * (int)sizeof(T) / 16;  // 16-byte chunks per plane row
-  constexpr int EPC = 16 / (int)sizeof(T);         // elements per chunk
-  const int nrows = r_end - r_begin;
-  const int total = nrows * 16 * CH;
-  for (int ci = threadIdx.x; ci < total; ci += NT) {
-    const int rr = ci / (16 * CH);
-    const int rem = ci - rr * 16 * CH;
-    const int k = rem / CH;
-    const int ch = rem - k * CH;
-    const int r = r_begin + rr;
-    T* dst = S.stage + (mod_pos(r, SROWS) * 16 + k) * SCOL + ch * EPC;
+__device__ __forceinline__ void stage_rows(const StepArgs<T>& P, const Smem<T>& S,
+                                           const StageSlots<T>& sl, int r_begin, int r_end) {
+  using SS = StageSlots<T>;
+  for (int r = r_begin; r < r_end; ++r) {
+    T* srow = S.stage + mod_pos(r, SROWS) * 16 * SCOL;
     if (P.walls && (r < 0 || r >= P.Ly)) {
-      const T gv = r < 0 ? P.v[k].gbot : P.v[k].gtop;
 #pragma unroll
-      for (int e = 0; e < EPC; ++e) dst[e] = gv;
+      for (int m = 0; m < SS::NS; ++m) {
+        const int c = threadIdx.x + NT * m;
+        if (c < SS::PER_ROW) {
+          const int k = c / SS::CH;
+          const T gv = r < 0 ? P.v[k].gbot : P.v[k].gtop;
+#pragma unroll
+          for (int e = 0; e < SS::EPC; ++e) srow[sl.dst[m] + e] = gv;
+        }
+      }
       continue;
     }
     const int rw = r < 0 ? r + P.Ly * ((-r + P.Ly - 1) / P.Ly) : (r >= P.Ly ? r % P.Ly : r);
-    const T* src_row = P.fin + (long long)k * P.plane + (long long)rw * P.Lx;
-    if (VEC) {
-      const int gg = (ch * EPC) >> 2, within = (ch * EPC) & 3;
-      cp_async16(dst, src_row + S.col[gg] + within);
-    } else {
-      const int x0 = S.col[0];  // unwrapped first staging column (scalar path)
+    const T* frow = P.fin + (long long)rw * P.Lx;
 #pragma unroll
-      for (int e = 0; e < EPC; ++e) dst[e] = __ldg(src_row + wrapi(x0 + ch * EPC + e, P.Lx));
+    for (int m = 0; m < SS::NS; ++m) {
+      const int c = threadIdx.x + NT * m;
+      if (c < SS::PER_ROW) {
+        if (VEC) {
+          cp_async16(srow + sl.dst[m], frow + sl.src[m]);
+        } else {
+          const int k = c / SS::CH, ch = c - k * SS::CH;
+          const T* fk = frow + (long long)k * P.plane;
+          const int x0 = S.col[0];  // unwrapped first staging column (scalar path)
+#pragma unroll
+          for (int e = 0; e < SS::EPC; ++e)
+            srow[sl.dst[m] + e] = __ldg(fk + wrapi(x0 + ch * SS::EPC + e, P.Lx));
+        }
+      }
     }
   }
 }
@@ -91,27 +125,29 @@ __device__ __forceinline__ void stage_rows(const StepArgs<T>& P, const Smem<T>& 
 // trip so that the two-row history rotates by register renaming.
 template <int SX, int SY, int ORDER, int LIM, typename T>
 __device__ __forceinline__ void advect_rows(const StepArgs<T>& P, const Smem<T>& S,
-                                            AdvState<T>& st, const VelConst<T>& vc, int a0, int k,
-                                            int g) {
+                                            AdvState<T>& st, const VelConst<T>& vc, int a0,
+                                            int src_off, int dst_off, bool ghosts) {
   constexpr int LAG = SY > 0 ? 1 : 2;  // staged row read for output row a
+  int slot = mod_pos(a0 + LAG, SROWS);
 #pragma unroll 1
   for (int j = 0; j < RPI; j += 2) {
 #pragma unroll
     for (int jj = 0; jj < 2; ++jj) {
       const int a = a0 + j + jj;
       T v[12];
-      const T* srow = S.stage + (mod_pos(a + LAG, SROWS) * 16 + k) * SCOL + 4 * g;
+      const T* srow = S.stage + slot * (16 * SCOL) + src_off;
+      slot = slot == SROWS - 1 ? 0 : slot + 1;
       sload4(srow, v);
       sload4(srow + 4, v + 4);
       sload4(srow + 8, v + 8);
       T out[4];
       advect_row<SX, SY, ORDER, LIM>(st, v, vc, out);
-      if (P.walls && (a < 0 || a >= P.Ly)) {  // ghost rows keep f^eq(rho_ext, u_wall)
+      if (ghosts && (a < 0 || a >= P.Ly)) {  // ghost rows keep f^eq(rho_ext, u_wall)
         const T gv = a < 0 ? vc.gbot : vc.gtop;
 #pragma unroll
         for (int i = 0; i < 4; ++i) out[i] = gv;
       }
-      T* dst = S.fs + ((a & (FROWS - 1)) * 16 + k) * REG + 4 * g;
+      T* dst = S.fs + (a & (FROWS - 1)) * (16 * REG) + dst_off;
       if constexpr (sizeof(T) == 4) {
         *reinterpret_cast<float4*>(dst) = make_float4(out[0], out[1], out[2], out[3]);
       } else {
@@ -122,12 +158,12 @@ __device__ __forceinline__ void advect_rows(const StepArgs<T>& P, const Smem<T>&
   }
 }
 
+// One row segment [ys, ye) of one strip of one lattice.  Every node's update
+// uses the same arithmetic in the same order whatever the segment boundaries,
+// so results do not depend on how the rows are split over CTAs or lattices.
 template <typename T, int ORDER, int LIM, bool VEC>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
-    step_kernel(const __grid_constant__ StepArgs<T> P) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Smem<T> S(smem_raw);
-
+__device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T>& S, int strip,
+                                            int ys, int ye) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int q = warp & 3;                          // sign quadrant of the warp
@@ -135,15 +171,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
   const int k = ((lane >> 3) << 2) | q;            // velocity of this thread in P1
   const VelConst<T> vc = P.v[k];
   const int Lx = P.Lx, Ly = P.Ly;
-
-  long long r0 = (long long)blockIdx.x * P.rows_per_cta;
-  const long long r1 = min(r0 + P.rows_per_cta, P.rows_total);
-
-  while (r0 < r1) {
-    const int strip = (int)(r0 / Ly);
-    const int ys = (int)(r0 % Ly);
-    const int ye = (int)min((long long)Ly, (long long)ys + (r1 - r0));
-    r0 += ye - ys;
+  {
 
     // wrapped global columns of the staging groups (region column 0 is global
     // column strip*TW - XOFF; the first staging column is region column -4)
@@ -166,24 +194,29 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     const int p4_x = strip * TW + p4_col - XOFF;            // global output column
     const bool p4_col_ok = p4_col < XOFF + TW && p4_x < Lx;
 
+    const StageSlots<T> slots(P, S, VEC);
     int a0 = ys - WARMUP;
-    stage_rows<T, VEC>(P, S, a0 + 1, a0 + RPI + 2, strip);
+    stage_rows<T, VEC>(P, S, slots, a0 + 1, a0 + RPI + 2);
     cp_async_commit();
 
     for (; a0 - 2 < ye; a0 += RPI) {
       // ---------------- L: prefetch the rows only the next iteration needs
       const bool more = (a0 + RPI) - 2 < ye;
-      if (more) stage_rows<T, VEC>(P, S, a0 + RPI + 2, a0 + 2 * RPI + 2, strip);
+      if (more) stage_rows<T, VEC>(P, S, slots, a0 + RPI + 2, a0 + 2 * RPI + 2);
       cp_async_commit();
       cp_async_wait<1>();
       __syncthreads();
 
       // ---------------- P1: advect rows a0 .. a0+RPI-1 of plane k
-      switch (q) {
-        case 0: advect_rows<+1, +1, ORDER, LIM>(P, S, st, vc, a0, k, g); break;
-        case 1: advect_rows<-1, +1, ORDER, LIM>(P, S, st, vc, a0, k, g); break;
-        case 2: advect_rows<-1, -1, ORDER, LIM>(P, S, st, vc, a0, k, g); break;
-        default: advect_rows<+1, -1, ORDER, LIM>(P, S, st, vc, a0, k, g); break;
+      {
+        const bool ghosts = P.walls && (a0 < 0 || a0 + RPI > Ly);  // any wall ghost row here
+        const int so = k * SCOL + 4 * g, dof = k * REG + 4 * g;
+        switch (q) {
+          case 0: advect_rows<+1, +1, ORDER, LIM>(P, S, st, vc, a0, so, dof, ghosts); break;
+          case 1: advect_rows<-1, +1, ORDER, LIM>(P, S, st, vc, a0, so, dof, ghosts); break;
+          case 2: advect_rows<-1, -1, ORDER, LIM>(P, S, st, vc, a0, so, dof, ghosts); break;
+          default: advect_rows<+1, -1, ORDER, LIM>(P, S, st, vc, a0, so, dof, ghosts); break;
+        }
       }
       __syncthreads();
 
@@ -235,6 +268,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
       // ---------------- P4: g, collision of all planes, store (rows a0-2 .. a0+1)
       {
         const int c = a0 - 2 + p4_row;
+        T rho_post = T(-1);  // post-step density of this thread's node, if it has one
         if (p4_col_ok && c >= ys && c < ye) {
           const int col = p4_col;
           const int sc = (c & (MROWS - 1)) * REG + col;
@@ -315,12 +349,18 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
             if (dx * dx + dy * dy > P.rbc2) scale = P.rho_ext * ir;
           }
 
+          rho_post = scale * rho;  // the collision conserves mass; the reservoir rescales it
           T* dst = P.fout + (long long)c * Lx + p4_x;
+          const long long pl = P.plane;
+          const T add = P.reservoir ? P.rho_ref * (scale - T(1)) : T(0);
+          if (!P.reservoir) scale = T(1);
 #pragma unroll
           for (int grp = 0; grp < 4; ++grp) {
             const ClassConst<T>& cl = P.cls[grp];
             const int ix = grp & 1, iy = grp >> 1;  // magnitude index (0 lo, 1 hi) in x, y
             const T P0 = p0 + cl.omA, P1 = p1 + cl.Ak, K1c = p2 + cl.omB, wr = cl.w * rho;
+            const T sw = scale * wr, radd = cl.w * add;
+            const T s1 = scale * P.one_m_omega;
 #pragma unroll
             for (int sgn = 0; sgn < 4; ++sgn) {
               const int kk = 4 * grp + sgn;
@@ -332,14 +372,106 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
               const T K2 = T(0.5) * D + P.om2;
               // (omega f^eq + dt F_k - omega w rho_ref) / (w rho): a cubic in xi.u
               const T poly = K0 + cu * (K1 + cu * (K2 + cu * P.om6));
-              T fn = P.one_m_omega * base[kk] + wr * poly;
-              if (P.reservoir) fn = scale * fn + cl.w * P.rho_ref * (scale - T(1));
-              dst[(long long)kk * P.plane] = fn;
+              // f^{n+1} = (1 - omega) f* + w rho poly, then the reservoir rescale
+              // s f + w rho_ref (s - 1) outside R_BC (s = 1, add = 0 elsewhere)
+              *dst = s1 * base[kk] + (sw * poly + radd);
+              dst += pl;
             }
+          }
+        }
+        if (P.diag_mass) {  // fused diagnostics: warp sums, then per-CTA shared accumulators
+          const bool on = rho_post >= T(0);
+          const bool in = on && rho_post < P.diag_thr;
+          const unsigned long long i = in ? (unsigned long long)p4_x : 0ULL;
+          const unsigned long long j = in ? (unsigned long long)c : 0ULL;
+          double m = on ? (double)rho_post : 0.0;
+          unsigned long long v[6] = {in ? 1ULL : 0ULL, i, j, i * i, i * j, j * j};
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            m += __shfl_down_sync(0xffffffffu, m, o);
+#pragma unroll
+            for (int t = 0; t < 6; ++t) v[t] += __shfl_down_sync(0xffffffffu, v[t], o);
+          }
+          if (lane == 0) {
+            atomicAdd(S.dmass, m);
+#pragma unroll
+            for (int t = 0; t < 6; ++t) atomicAdd(&S.dsums[t], v[t]);
           }
         }
       }
     }
     cp_async_wait<0>();
   }
+}
+
+// Work items are (row block, strip) pairs in row-block-major order, claimed
+// from a device counter: CTAs that run at the same time work on the same rows
+// of neighbouring strips, so the halo columns they share and the output lines
+// they both write meet in L2.  The last CTA to finish resets the counters, so
+// the next launch (or a replay of a captured graph) starts from zero.
+__device__ __forceinline__ long long claim_item(unsigned long long* sched, long long* s_item) {
+  __syncthreads();  // everyone has read the previous item
+  if (threadIdx.x == 0) *s_item = (long long)atomicAdd(&sched[0], 1ULL);
+  __syncthreads();
+  return *s_item;
+}
+__device__ __forceinline__ void retire_cta(unsigned long long* sched) {
+  if (threadIdx.x == 0) {
+    const unsigned long long done = atomicAdd(&sched[1], 1ULL);
+    if (done == gridDim.x - 1) {
+      sched[0] = 0ULL;
+      sched[1] = 0ULL;
+    }
+  }
+}
+
+template <typename T, int ORDER, int LIM, bool VEC>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+    step_kernel(const __grid_constant__ StepArgs<T> P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Smem<T> S(smem_raw);
+  __shared__ long long s_item;
+  if (threadIdx.x == 0) {
+    *S.dmass = 0.0;
+    for (int t = 0; t < 6; ++t) S.dsums[t] = 0ULL;
+  }
+  for (;;) {
+    const long long item = claim_item(P.sched, &s_item);
+    if (item >= P.items) break;
+    const long long rb = item / P.nstrip;
+    const int strip = (int)(item - rb * P.nstrip);
+    const int ys = (int)(rb * P.row_block);
+    const int ye = min(P.Ly, ys + P.row_block);
+    run_segment<T, ORDER, LIM, VEC>(P, S, strip, ys, ye);
+  }
+  // claim_item's barrier after the last claim orders every warp's shared adds
+  if (P.diag_mass && threadIdx.x == 0) {
+    atomicAdd(P.diag_mass, *S.dmass);
+    for (int t = 0; t < 6; ++t) atomicAdd(&P.diag_sums[t], S.dsums[t]);
+  }
+  retire_cta(P.sched);
+}
+
+// Several lattices advanced by one launch: their work items are concatenated
+// and claimed from one counter.
+template <typename T, int ORDER, int LIM, bool VEC>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+    step_batch_kernel(const __grid_constant__ BatchArgs<T> B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Smem<T> S(smem_raw);
+  __shared__ long long s_item;
+  int i = 0;
+  for (;;) {
+    const long long item = claim_item(B.sched, &s_item);
+    if (item >= B.item_start[B.count]) break;
+    while (B.item_start[i + 1] <= item) ++i;
+    const StepArgs<T>& P = B.L[i];
+    const long long local = item - B.item_start[i];
+    const long long rb = local / P.nstrip;
+    const int strip = (int)(local - rb * P.nstrip);
+    const int ys = (int)(rb * P.row_block);
+    const int ye = min(P.Ly, ys + P.row_block);
+    run_segment<T, ORDER, LIM, VEC>(P, S, strip, ys, ye);
+  }
+  retire_cta(B.sched);
 }

@@ -190,3 +190,69 @@ def test_zero_steps_and_step_count(P):
         assert np.array_equal(L.get_f(), f0) and L.step_count == 0
         L.step(3)
         assert L.step_count == 3
+
+
+def test_step_many_matches_stepping_alone(P):
+    """Lattices of different sizes and physics stepped by one batched launch per
+    step end where they end when stepped alone, to FP32 rounding (the batched
+    and single kernels are compiled separately, so the compiler may fuse
+    multiply-adds differently); an FP64 lattice in the list steps on its own and
+    is bitwise equal."""
+    import torch
+    from paper_1802_01272_gb300.binding import step_many
+    stream = torch.cuda.current_stream()
+    specs = [
+        dict(Lx=256, Ly=200, T=0.9, tau=1e-3),
+        dict(Lx=512, Ly=96, T=0.8, tau=1e-2, boundary=P.LBM_BC_SHEAR_WALLS, rho_ext=1.9,
+             shear_rate=2 * 0.2 / (96 / 256.0)),
+        dict(Lx=128, Ly=300, T=0.95, tau=2e-3),
+        dict(Lx=64, Ly=64, T=0.9, precision=P.LBM_FP64),
+    ]
+    def make(spec, seed):
+        lp = P.Params(rho_ref=1.2, **spec)
+        L = P.Lattice(lp, stream)
+        rho, ux, uy = synth.bubble(lp.Lx, lp.Ly, 1.5, 0.6, R=min(lp.Lx, lp.Ly) / 5, W=2)
+        L.init_rho_u(rho * (1 + 1e-3 * synth.normal(seed, lp.Lx * lp.Ly).reshape(rho.shape)),
+                     ux, uy)
+        return L
+    alone = [make(s, i) for i, s in enumerate(specs)]
+    mixed = [make(s, i) for i, s in enumerate(specs)]
+    for L in alone:
+        L.step(9)
+    step_many(mixed, 4)
+    step_many(mixed, 5)
+    for A, B in zip(alone, mixed):
+        assert A.step_count == B.step_count == 9
+        fa, fb = A.get_f(), B.get_f()
+        if A.params.precision == P.LBM_FP64:
+            assert np.array_equal(fa, fb)
+        else:
+            err = rel_err(fb, fa)
+            print(f"batched vs alone {A.params.Lx}x{A.params.Ly}: {err:.2e}")
+            assert err < 1e-5
+    for L in alone + mixed:
+        L.close()
+
+
+def test_step_diag_fused_record_matches_full_diagnostics(P):
+    """Diagnostics reduced inside the last step equal the separate reduction of
+    the state after it (FP64: same sites, same integer sums, mass to rounding)."""
+    for prec, tol in ((P.LBM_FP64, 1e-12), (P.LBM_FP32_SHIFTED, 1e-6)):
+        lp = P.Params(Lx=300, Ly=260, precision=prec, T=0.8, rho_ref=1.9, rho_ext=1.9,
+                      boundary=P.LBM_BC_SHEAR_WALLS, shear_rate=2 * 0.1 / (260 / 256.0))
+        rho, ux, uy = synth.bubble(300, 260, 1.9, 0.24, R=40, W=3)
+        thr = 0.5 * (1.9 + 0.24)
+        with P.Lattice(lp) as L:
+            L.init_rho_u(rho, ux, uy)
+            d = L.step_diag(6, thr)
+            full = L.diagnostics(thr)
+            assert L.step_count == 6
+        assert abs(d["mass"] - full["mass"]) / full["mass"] < tol
+        if prec == P.LBM_FP64:
+            for n in ("nb", "sx", "sy", "sxx", "sxy", "syy"):
+                assert d[n] == full[n]
+        else:
+            assert abs(d["nb"] - full["nb"]) <= 2
+        for n in ("a", "b", "D"):
+            assert abs(d[n] - full[n]) < 1e-2 * max(1.0, abs(full[n]))
+        assert np.isnan(d["rho_min"]) and not np.isnan(full["rho_min"])

@@ -1,0 +1,119 @@
+"""Physics validation of the CUDA path against numbers the paper prints.
+
+* Table II: apparent viscosity of axial and diagonal shear waves (lambda = 2,
+  U = 0.01, rho = 1, T = 1, F = 0, dt = 1e-4) for CTU1 and CTU2.
+* Sec. II E: liquid and vapour densities of a phase-separated van der Waals
+  fluid against the Maxwell construction, and FP32 shifted storage against
+  FP64 on the same run.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from tests.conftest import has_gpu
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not has_gpu(), reason="needs a CUDA GPU")]
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+ROWS = GOLD["table_II_apparent_viscosity"]["rows"]   # tau, ds, c1a, c2a, c1d, c2d
+
+
+def shear_wave_viscosity(P, order, tau, ds, diagonal, t1, t2, precision):
+    """Decay rate of u_perp between t1 and t2 (Eq. avisco between two times)."""
+    if diagonal:
+        L = int(round(2 * math.sqrt(2) / ds))       # 362 at ds = 1/128 (as the paper)
+        kx = ky = 2 * math.pi / (L * ds)            # exactly periodic, lambda = L ds / sqrt 2
+        Lx, Ly = L, L
+    else:
+        Lx, Ly = int(round(2 / ds)), 16
+        kx, ky = 2 * math.pi / (Lx * ds), 0.0
+    lp = P.Params(Lx=Lx, Ly=Ly, a=0.0, b=0.0, kappa=0.0, T=1.0, tau=tau, dt=1e-4, ds=ds,
+                  ctu_order=order, precision=precision, rho_ref=1.0)
+    rho, ux, uy = synth.shear_wave(Lx, Ly, ds, 0.01, kx, ky)
+    k2 = kx * kx + ky * ky
+    ex, ey = -ky / math.sqrt(k2), kx / math.sqrt(k2)
+    with P.Lattice(lp) as L_:
+        L_.init_rho_u(rho, ux, uy)
+        L_.step(int(round(t1 / 1e-4)))
+        _, a, b = L_.moments()
+        u1 = a[0, 0] * ex + b[0, 0] * ey
+        L_.step(int(round((t2 - t1) / 1e-4)))
+        _, a, b = L_.moments()
+        u2 = a[0, 0] * ex + b[0, 0] * ey
+    return math.log(u1 / u2) / (k2 * (t2 - t1))
+
+
+@pytest.mark.parametrize("row", range(4), ids=lambda r: f"tau{ROWS[r][0]}_ds{ROWS[r][1]:.5f}")
+@pytest.mark.parametrize("order", [1, 2])
+def test_table_II_axial(row, order):
+    import paper_1802_01272_gb300 as P
+    tau, ds = ROWS[row][0], ROWS[row][1]
+    want = ROWS[row][2] if order == 1 else ROWS[row][3]
+    # CTU1 settles within a few tau; the MC limiter of CTU2 reshapes the wave
+    # slowly, so its rate is read from t = 1 on (see the oracle pin)
+    t1, t2 = (0.05, 0.5) if order == 1 else (1.0, 2.0)
+    nu = shear_wave_viscosity(P, order, tau, ds, False, t1, t2, P.LBM_FP64)
+    print(f'\nTableII axial order={order} tau={tau} ds={ds}: nu={nu:.6e} paper={want:.6e} rel={(nu-want)/want:+.2e}')
+    assert abs(nu - want) / want < 1e-3, (nu, want)
+
+
+@pytest.mark.parametrize("order,col", [(1, 4), (2, 5)])
+def test_table_II_diagonal(order, col):
+    """Diagonal waves on the 362 x 362 lattice of the paper exercise the transverse
+    terms of CTU2; FP64 storage (FP32 storage adds a slow systematic drift of
+    ~1e-9 per step from its rounded quadrature constants, visible over the
+    2e4 steps of this measurement)."""
+    import paper_1802_01272_gb300 as P
+    tau, ds = ROWS[0][0], ROWS[0][1]
+    t1, t2 = (0.05, 0.5) if order == 1 else (1.0, 2.0)
+    nu = shear_wave_viscosity(P, order, tau, ds, True, t1, t2, P.LBM_FP64)
+    want = ROWS[0][col]
+    print(f'\nTableII diagonal order={order}: nu={nu:.6e} paper={want:.6e} rel={(nu-want)/want:+.2e}')
+    assert abs(nu - want) / want < 2e-3, (nu, want)
+
+
+def spinodal(P, T, precision, steps, L=512, seed=1):
+    lp = P.Params(Lx=L, Ly=L, T=T, precision=precision, rho_ref=1.0)
+    rho, ux, uy = synth.noisy_uniform(L, L, 1.0, 1e-2, seed=seed)
+    with P.Lattice(lp) as L_:
+        L_.init_rho_u(rho, ux, uy)
+        L_.step(steps)
+        r, _, _ = L_.moments()
+        h = L_.histogram(2048, 0.0, 3.0)
+    return r, h
+
+
+def test_spinodal_coexistence_matches_maxwell():
+    """Sec. II E: the phase-separated fluid sits at the Maxwell densities
+    (the paper reports agreement for T >= 0.7; tau = 1e-3, ds = 1/256)."""
+    import paper_1802_01272_gb300 as P
+    from oracle import analysis as A
+    T = 0.9
+    r, h = spinodal(P, T, P.LBM_FP32_SHIFTED, 20000)
+    rl, rv = A.coexistence_from_histogram(h, 0.0, 3.0, rho_values=r.ravel())
+    ml, mv = A.maxwell(T)
+    print(f'\nspinodal T={T}: rho_L={rl:.6f} rho_V={rv:.6f} maxwell {ml:.6f} {mv:.6f} rel {(rl-ml)/ml:+.2e} {(rv-mv)/mv:+.2e}')
+    assert abs(rl - ml) / ml < 1e-2 and abs(rv - mv) / mv < 2e-2, (rl, rv, ml, mv)
+
+
+def test_fp32_shifted_coexistence_matches_fp64():
+    """FP32 shifted storage against FP64 on the same run: rho within 1e-5
+    after 1000 steps and coexistence densities within 1e-4."""
+    import paper_1802_01272_gb300 as P
+    from oracle import analysis as A
+    T, L = 0.8, 256
+    r32, _ = spinodal(P, T, P.LBM_FP32_SHIFTED, 1000, L=L)
+    r64, _ = spinodal(P, T, P.LBM_FP64, 1000, L=L)
+    print(f'\nfp32 vs fp64 rho after 1000 steps: {np.abs(r32 - r64).max() / np.abs(r64).max():.2e}')
+    assert np.abs(r32 - r64).max() / np.abs(r64).max() < 1e-5
+    r32, h32 = spinodal(P, T, P.LBM_FP32_SHIFTED, 6000, L=L)
+    r64, h64 = spinodal(P, T, P.LBM_FP64, 6000, L=L)
+    c32 = A.coexistence_from_histogram(h32, 0.0, 3.0, rho_values=r32.ravel())
+    c64 = A.coexistence_from_histogram(h64, 0.0, 3.0, rho_values=r64.ravel())
+    print(f'\ncoexistence fp32 {c32} fp64 {c64}')
+    for a, b in zip(c32, c64):
+        assert abs(a - b) / b < 1e-4, (c32, c64)

@@ -476,3 +476,15 @@ def test_rayleigh_plesset_static_bubble_and_rk4():
     sol = solve_ivp(lambda tt, y: A.rp_rhs(tt, y, **kw), (0, 2.0), [0.3, 0.0], rtol=1e-11,
                     atol=1e-13, t_eval=[2.0])
     assert R[-1] > 0.31 and abs(R[-1] - sol.y[0, -1]) < 1e-9
+
+
+def test_library_eos_helpers_agree_with_oracle():
+    """The run-setup helpers of the library (equal-area rule) against the oracle's
+    closed forms (equal pressure and chemical potential): two routes, one answer."""
+    from oracle import analysis as A
+    from paper_1802_01272_gb300 import eos
+    for T in (0.7, 0.8, 0.9, 0.95, 0.98):
+        rl, rv = eos.coexistence(T)
+        ml, mv = A.maxwell(T)
+        assert abs(rl - ml) < 1e-9 and abs(rv - mv) < 1e-9
+    assert abs(eos.interface_tension(0.8, 1e-4) - A.sigma_exact(0.8, 1e-4)) < 1e-10

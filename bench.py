@@ -79,9 +79,12 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ("lbm_kernels.cuh", "step_kernel_body.cuh", "step_fp32.cu", "step_fp64.cu")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("lbm_kernels.cuh", "step_fp32.cu", "step_fp64.cu"):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_1802_01272_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

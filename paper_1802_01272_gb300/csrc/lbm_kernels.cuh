@@ -181,18 +181,30 @@ __device__ __forceinline__ void sload4(const T* p, T* v) {
 }
 
 // ------------------------------------------------------ advection state
-// Columns: the thread owns group columns 0..3.  CTU keeps five columns C5 =
-// {own, own - sgn_x}: for sgn_x > 0 relative columns -1..3, else 0..4.
+// Columns: the thread owns group columns 0..3.  f keeps five columns C5 =
+// {own, own - sgn_x} (relative -1..3 for sgn_x > 0, else 0..4), loaded from
+// the staged row.  Jumps, limited corrections and their differences are kept
+// for the own four columns only: the value a stencil needs one column beyond
+// the group is the neighbouring group's, taken from the adjacent lane (the 16
+// groups of a velocity sit on 16 consecutive lanes).  At the two region edges
+// that lane holds nothing useful; those columns (region 0 and 63) feed only
+// rho* outside the stencils of the strip's outputs.
 template <typename T>
 struct AdvState {
   T F0[5], F1[5];  // f on row a and on the y-upwind row a - sgn_y
-  T RY[5];         // sgn_y > 0: R^y(a);  sgn_y < 0: R^y(a+1)
-  T SY[5];         // half-limited S^y(a)
+  T RY[4];         // sgn_y > 0: R^y(a);  sgn_y < 0: R^y(a+1)
+  T SY[4];         // half-limited S^y(a)
   T A0[4], A1[4];  // x-differences of half-limited S^x on row a and on row a - sgn_y
 };
 
+__device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl_up1(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl_dn1(double v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+
 // One advection row for velocity k of quadrant (SX, SY).  `v` holds the newly
-// loaded row (a+1 if SY > 0, a+2 if SY < 0) at relative columns -4..7.
+// loaded row (a+1 if SY > 0, a+2 if SY < 0) at relative columns -4..7.  All 32
+// lanes of the warp must call it together (it exchanges neighbour columns).
 template <int SX, int SY, int ORDER, int LIM, typename T>
 __device__ __forceinline__ void advect_row(AdvState<T>& s, const T* v, const VelConst<T>& c,
                                            T* out) {
@@ -201,29 +213,33 @@ __device__ __forceinline__ void advect_row(AdvState<T>& s, const T* v, const Vel
 #pragma unroll
   for (int m = 0; m < 5; ++m) Fn[m] = v[4 + B5 + m];
 
-  T Bv[5], An[4];
+  T Bv[4], Bu = T(0), An[4];
   if constexpr (ORDER == 2) {
-    T RYn[5], SYn[5];
+    T RYn[4], SYn[4];
 #pragma unroll
-    for (int m = 0; m < 5; ++m) {
+    for (int i = 0; i < 4; ++i) {
+      const int mo = i - B5;
       if constexpr (SY > 0) {
-        RYn[m] = Fn[m] - s.F0[m];                     // R^y(a+1)
-        SYn[m] = half_limited<LIM>(RYn[m], s.RY[m]);  // S^y(a+1), upwind R^y(a)
+        RYn[i] = Fn[mo] - s.F0[mo];                   // R^y(a+1)
+        SYn[i] = half_limited<LIM>(RYn[i], s.RY[i]);  // S^y(a+1), upwind R^y(a)
       } else {
-        RYn[m] = Fn[m] - s.F1[m];                     // R^y(a+2)
-        SYn[m] = half_limited<LIM>(s.RY[m], RYn[m]);  // S^y(a+1), upwind R^y(a+2)
+        RYn[i] = Fn[mo] - s.F1[mo];                   // R^y(a+2)
+        SYn[i] = half_limited<LIM>(s.RY[i], RYn[i]);  // S^y(a+1), upwind R^y(a+2)
       }
-      Bv[m] = SYn[m] - s.SY[m];                       // S^y(a+1) - S^y(a)
-      s.RY[m] = RYn[m];
-      s.SY[m] = SYn[m];
+      Bv[i] = SYn[i] - s.SY[i];                       // S^y(a+1) - S^y(a)
+      s.RY[i] = RYn[i];
+      s.SY[i] = SYn[i];
     }
-    // x direction on the new row: R^x(c) = f(c) - f(c-1) for c in -1..5
+    // B one column upwind in x: the neighbouring group's edge column
+    if constexpr (SX > 0) Bu = shfl_up1(Bv[3]); else Bu = shfl_dn1(Bv[0]);
+    // x direction on the new row: R^x(c) = f(c) - f(c-1)
     T RX[7];
 #pragma unroll
     for (int j = 0; j < 7; ++j) RX[j] = v[3 + j] - v[2 + j];  // RX[j] = R^x(j-1)
     T SXh[5];
 #pragma unroll
-    for (int m = 0; m < 5; ++m) SXh[m] = half_limited<LIM>(RX[m + 1], RX[m + 1 - SX]);
+    for (int m = 0; m < 4; ++m) SXh[m] = half_limited<LIM>(RX[m + 1], RX[m + 1 - SX]);
+    SXh[4] = shfl_dn1(SXh[0]);                         // column 4 = next group's column 0
 #pragma unroll
     for (int i = 0; i < 4; ++i) An[i] = SXh[i + 1] - SXh[i];
   }
@@ -235,8 +251,10 @@ __device__ __forceinline__ void advect_row(AdvState<T>& s, const T* v, const Vel
     const int mu = i - SX - B5;  // x-upwind column in C5
     T u1 = c.c00 * s.F0[mo] + c.c10 * s.F0[mu] + c.c01 * s.F1[mo] + c.c11 * s.F1[mu];
     if constexpr (ORDER == 2) {
+      const int iu = i - SX;     // x-upwind column among the own four (or the neighbour's)
+      const T bu = (iu >= 0 && iu < 4) ? Bv[iu >= 0 && iu < 4 ? iu : 0] : Bu;
       u1 -= c.a1 * s.A0[i] + c.a2 * s.A1[i];
-      u1 -= c.b1 * Bv[mo] + c.b2 * Bv[mu];
+      u1 -= c.b1 * Bv[i] + c.b2 * bu;
     }
     out[i] = u1;
   }

@@ -166,9 +166,11 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T>&
                                             int ys, int ye) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int q = warp & 3;                          // sign quadrant of the warp
-  const int g = ((warp >> 2) << 3) | (lane & 7);   // column group 0..15
-  const int k = ((lane >> 3) << 2) | q;            // velocity of this thread in P1
+  // P1 layout: a warp = one sign quadrant x two velocity groups x 16 column
+  // groups, so column neighbours are adjacent lanes
+  const int q = warp & 3;                               // sign quadrant of the warp
+  const int g = lane & 15;                              // column group 0..15
+  const int k = ((((warp >> 2) << 1) | (lane >> 4)) << 2) | q;  // velocity of this thread
   const VelConst<T> vc = P.v[k];
   const int Lx = P.Lx, Ly = P.Ly;
   {
@@ -184,9 +186,9 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T>&
 
     AdvState<T> st;
 #pragma unroll
-    for (int m = 0; m < 5; ++m) st.F0[m] = st.F1[m] = st.RY[m] = st.SY[m] = T(0);
+    for (int m = 0; m < 5; ++m) st.F0[m] = st.F1[m] = T(0);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) st.A0[i] = st.A1[i] = T(0);
+    for (int i = 0; i < 4; ++i) st.RY[i] = st.SY[i] = st.A0[i] = st.A1[i] = T(0);
 
     // P4 thread -> node mapping: a warp pair per row, 32 + 24 output columns
     const int p4_row = warp >> 1;                           // 0..3 within the iteration
@@ -382,20 +384,23 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T>&
         if (P.diag_mass) {  // fused diagnostics: warp sums, then per-CTA shared accumulators
           const bool on = rho_post >= T(0);
           const bool in = on && rho_post < P.diag_thr;
-          const unsigned long long i = in ? (unsigned long long)p4_x : 0ULL;
-          const unsigned long long j = in ? (unsigned long long)c : 0ULL;
           double m = on ? (double)rho_post : 0.0;
-          unsigned long long v[6] = {in ? 1ULL : 0ULL, i, j, i * i, i * j, j * j};
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            m += __shfl_down_sync(0xffffffffu, m, o);
+          for (int o = 16; o > 0; o >>= 1) m += __shfl_down_sync(0xffffffffu, m, o);
+          if (lane == 0) atomicAdd(S.dmass, m);
+          if (__ballot_sync(0xffffffffu, in)) {  // bubble sites are rare: sum them only here
+            const unsigned long long i = in ? (unsigned long long)p4_x : 0ULL;
+            const unsigned long long j = in ? (unsigned long long)c : 0ULL;
+            unsigned long long v[6] = {in ? 1ULL : 0ULL, i, j, i * i, i * j, j * j};
 #pragma unroll
-            for (int t = 0; t < 6; ++t) v[t] += __shfl_down_sync(0xffffffffu, v[t], o);
-          }
-          if (lane == 0) {
-            atomicAdd(S.dmass, m);
+            for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-            for (int t = 0; t < 6; ++t) atomicAdd(&S.dsums[t], v[t]);
+              for (int t = 0; t < 6; ++t) v[t] += __shfl_down_sync(0xffffffffu, v[t], o);
+            }
+            if (lane == 0) {
+#pragma unroll
+              for (int t = 0; t < 6; ++t) atomicAdd(&S.dsums[t], v[t]);
+            }
           }
         }
       }

@@ -78,7 +78,7 @@ WINDOWS = [
     (0, 100, 12, 24, True, False),          # bottom wall
     (6144 - 12, 3000, 12, 24, False, True),  # top wall
     (2000, 6144 - 10, 16, 24, False, False),  # periodic x seam
-    (4000, 60 * 51 - 8, 16, 24, False, False),  # strip seam of the kernel (60-column strips)
+    (4000, 56 * 55 - 8, 16, 24, False, False),  # strip seam of the kernel (56-column strips)
     (3072 - 30, 3072 - 12, 24, 24, False, False),  # bubble interface (R = 26 nodes)
     (1234, 777, 16, 20, False, False),
 ]

@@ -199,6 +199,22 @@ int lbm_sync(lbm_handle* h);
 /* Number of steps taken since the last init / set. */
 int64_t lbm_step_count(const lbm_handle* h);
 
+/* Launch geometry of the handle's fused step kernel (no counterpart in the
+ * paper: for tuning, benchmarking and tests).
+ *   grid          CTAs of the persistent launch (SMs x resident CTAs at most)
+ *   threads       threads per CTA
+ *   smem_bytes    dynamic shared memory per CTA
+ *   strips        strips of 56 output columns across x
+ *   row_block     rows per work item (work items = strips x row blocks)
+ *   tensor_copies 1 when strips away from the periodic x seam stage f^n rows
+ *                 with tensor (TMA) copies, 0 when every strip uses per-thread
+ *                 16-byte copies (Lx not a multiple of 4, or Lx < 72)
+ * Returns LBM_ERR_INVALID_ARG for a null argument; the handle is not touched. */
+typedef struct lbm_kernel_info {
+  int32_t grid, threads, smem_bytes, strips, row_block, tensor_copies;
+} lbm_kernel_info;
+int lbm_get_kernel_info(const lbm_handle* h, lbm_kernel_info* out);
+
 /* Static description of a code. */
 const char* lbm_strerror(int code);
 

@@ -44,6 +44,11 @@ class lbm_params(C.Structure):
     ]
 
 
+class lbm_kernel_info(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in ("grid", "threads", "smem_bytes", "strips", "row_block",
+                                         "tensor_copies")]
+
+
 class lbm_diag(C.Structure):
     _fields_ = [
         ("mass", C.c_double), ("nb", C.c_int64), ("sx", C.c_int64), ("sy", C.c_int64),
@@ -59,7 +64,8 @@ EXPORTS = ["lbm_default_params", "lbm_create", "lbm_destroy", "lbm_init_rho_u", 
            "lbm_step_diag",
            "lbm_init_rho_u_device", "lbm_set_f", "lbm_get_f", "lbm_set_f_device",
            "lbm_get_f_device", "lbm_step", "lbm_moments", "lbm_moments_device",
-           "lbm_diagnostics", "lbm_histogram", "lbm_sync", "lbm_step_count", "lbm_strerror"]
+           "lbm_diagnostics", "lbm_histogram", "lbm_sync", "lbm_step_count", "lbm_strerror",
+           "lbm_get_kernel_info"]
 
 
 def lib_path() -> str:
@@ -92,6 +98,7 @@ def lib():
         L.lbm_sync.argtypes = [H]
         L.lbm_step_count.argtypes = [H]
         L.lbm_step_count.restype = i64
+        L.lbm_get_kernel_info.argtypes = [H, P(lbm_kernel_info)]
         L.lbm_histogram_noalloc.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double,
                                             C.c_int32, C.c_double, C.c_double, vp, P(C.c_int64)]
         L.lbm_strerror.argtypes = [C.c_int]
@@ -299,3 +306,9 @@ class Lattice:
     @property
     def step_count(self) -> int:
         return lib().lbm_step_count(self._h)
+
+    def kernel_info(self) -> dict:
+        """Launch geometry of the step kernel (lbm_get_kernel_info)."""
+        k = lbm_kernel_info()
+        _check(lib().lbm_get_kernel_info(self._h, C.byref(k)), "lbm_get_kernel_info")
+        return {n: getattr(k, n) for n, _ in lbm_kernel_info._fields_}

@@ -11,6 +11,8 @@
 #include <memory>
 #include <new>
 
+#include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled
+
 #include "ctulbm.h"
 #include "lbm_internal.h"
 
@@ -39,6 +41,7 @@ struct lbm_handle {
   double xi[16][2], w[16];
   StepArgs<float> a32;
   StepArgs<double> a64;
+  RowMaps tmap[2];  // tensor maps of f[0], f[1] (RPI-row and 1-row boxes)
   AuxArgs aux;
 };
 
@@ -69,6 +72,39 @@ void feq_host(const lbm_params& p, const double xi[16][2], const double w[16], d
              (1.0 + cu + 0.5 * (cu * cu - u2 + (T - 1.0) * (x2 - 2.0)) +
               cu / 6.0 * (cu * cu - 3.0 * u2 + 3.0 * (T - 1.0) * (x2 - 4.0)));
   }
+}
+
+// The driver's tensor-map encoder, resolved once through the runtime (the
+// library does not link the driver library itself).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// f [16][Ly][Lx] as a 3-D tensor ordered (x, plane, row), read in boxes of
+// SCOL columns x 16 planes x `rows` rows: the box lands in shared memory as
+// `rows` consecutive staged rows [16][SCOL].  False when the encoder is
+// unavailable or rejects the layout (the kernel then stages every strip by
+// per-thread copies).
+bool encode_row_map(void* base, size_t elem, int Lx, int Ly, int rows, CUtensorMap* out) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || Lx < SCOL || Ly < rows) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)Lx, 16, (cuuint64_t)Ly};
+  const cuuint64_t strides[2] = {(cuuint64_t)Lx * (cuuint64_t)Ly * elem, (cuuint64_t)Lx * elem};
+  const cuuint32_t box[3] = {(cuuint32_t)SCOL, 16, (cuuint32_t)rows};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(out, elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+             base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 int set_err(lbm_handle* h, int code) {
@@ -261,6 +297,7 @@ int check_device_error(lbm_handle* h) {
       cudaStreamSynchronize(h->stream) != cudaSuccess)
     return set_err(h, LBM_ERR_CUDA);
   if (e & 1u) set_err(h, LBM_ERR_NONFINITE);
+  if (e & 2u) set_err(h, LBM_ERR_TIMEOUT);
   return LBM_OK;
 }
 
@@ -352,6 +389,13 @@ int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out) {
     fill_step_args<float>(h, h->a32);
   else
     fill_step_args<double>(h, h->a64);
+  std::memset(h->tmap, 0, sizeof(h->tmap));
+  bool tma = h->vec;
+  for (int i = 0; i < 2 && tma; ++i)
+    tma = encode_row_map(h->f[i], h->elem, p->Lx, p->Ly, RPI, &h->tmap[i].m[0]) &&
+          encode_row_map(h->f[i], h->elem, p->Lx, p->Ly, 1, &h->tmap[i].m[1]);
+  h->a32.tma_ok = tma;
+  h->a64.tma_ok = tma;
   AuxArgs& x = h->aux;
   x.Lx = p->Lx;
   x.Ly = p->Ly;
@@ -469,11 +513,13 @@ int lbm_step(lbm_handle* h, int64_t n) {
     if (h->elem == 4) {
       h->a32.fin = static_cast<const float*>(h->f[h->cur]);
       h->a32.fout = static_cast<float*>(h->f[1 - h->cur]);
-      e = launch_step_f32(h->a32, h->p.ctu_order, lim, h->vec, h->grid, h->smem, h->stream);
+      e = launch_step_f32(h->a32, h->tmap[h->cur], h->p.ctu_order, lim, h->vec, h->grid, h->smem,
+                          h->stream);
     } else {
       h->a64.fin = static_cast<const double*>(h->f[h->cur]);
       h->a64.fout = static_cast<double*>(h->f[1 - h->cur]);
-      e = launch_step_f64(h->a64, h->p.ctu_order, lim, h->vec, h->grid, h->smem, h->stream);
+      e = launch_step_f64(h->a64, h->tmap[h->cur], h->p.ctu_order, lim, h->vec, h->grid, h->smem,
+                          h->stream);
     }
     if (e != cudaSuccess) return cuda_check(h, e);
     h->cur ^= 1;
@@ -572,7 +618,8 @@ int lbm_step_diag(lbm_handle* h, int64_t n, double threshold, lbm_diag* out) {
     a.diag_mass = &h->d_acc->mass;
     a.diag_sums = &h->d_acc->nb;
     a.diag_thr = (float)threshold;
-    e = launch_step_f32(a, h->p.ctu_order, lim, h->vec, h->grid, h->smem, h->stream);
+    e = launch_step_f32(a, h->tmap[h->cur], h->p.ctu_order, lim, h->vec, h->grid, h->smem,
+                        h->stream);
   } else {
     StepArgs<double> a = h->a64;
     a.fin = static_cast<const double*>(h->f[h->cur]);
@@ -580,7 +627,8 @@ int lbm_step_diag(lbm_handle* h, int64_t n, double threshold, lbm_diag* out) {
     a.diag_mass = &h->d_acc->mass;
     a.diag_sums = &h->d_acc->nb;
     a.diag_thr = threshold;
-    e = launch_step_f64(a, h->p.ctu_order, lim, h->vec, h->grid, h->smem, h->stream);
+    e = launch_step_f64(a, h->tmap[h->cur], h->p.ctu_order, lim, h->vec, h->grid, h->smem,
+                        h->stream);
   }
   if (e != cudaSuccess) return cuda_check(h, e);
   h->cur ^= 1;
@@ -655,6 +703,17 @@ int lbm_sync(lbm_handle* h) {
   h->sticky = LBM_OK;
   if (r == LBM_ERR_NONFINITE) cudaMemsetAsync(h->d_err, 0, sizeof(unsigned int), h->stream);
   return r;
+}
+
+int lbm_get_kernel_info(const lbm_handle* h, lbm_kernel_info* out) {
+  if (!h || !out) return LBM_ERR_INVALID_ARG;
+  out->grid = h->grid;
+  out->threads = NT;
+  out->smem_bytes = (int32_t)h->smem;
+  out->strips = h->nstrip;
+  out->row_block = h->row_block;
+  out->tensor_copies = h->elem == 4 ? h->a32.tma_ok : h->a64.tma_ok;
+  return LBM_OK;
 }
 
 int64_t lbm_step_count(const lbm_handle* h) { return h ? h->steps : -1; }

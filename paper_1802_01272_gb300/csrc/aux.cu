@@ -255,7 +255,10 @@ cudaError_t launch_hist(const AuxArgs& a, const void* f, int nbins, double lo, d
 
 size_t step_smem_bytes(size_t elem) {
   const size_t elems = (size_t)SROWS * 16 * SCOL + (size_t)FROWS * 16 * REG + 6 * (size_t)MROWS * REG;
-  return elem * elems + sizeof(int) * (SG + (SG & 1)) + sizeof(double) + 6 * sizeof(unsigned long long);
+  // + 128 bytes to align the staging ring for tensor copies; ints, the fused
+  // diagnostics accumulators, two mbarriers and the CTA's wait-abort flag
+  return 128 + elem * elems + sizeof(int) * (SG + (SG & 1)) + sizeof(double) +
+         6 * sizeof(unsigned long long) + 2 * sizeof(unsigned long long) + 2 * sizeof(int);
 }
 
 }  // namespace ctulbm

@@ -20,10 +20,11 @@ struct AuxArgs {
 };
 
 // One fused step kernel: returns cudaSuccess or the launch error.
-cudaError_t launch_step_f32(const StepArgs<float>& a, int order, int lim, bool vec, int grid,
-                            size_t smem, cudaStream_t s);
-cudaError_t launch_step_f64(const StepArgs<double>& a, int order, int lim, bool vec, int grid,
-                            size_t smem, cudaStream_t s);
+// `maps` describe a.fin (RowMaps); they are read only when a.tma_ok.
+cudaError_t launch_step_f32(const StepArgs<float>& a, const RowMaps& maps, int order, int lim,
+                            bool vec, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_step_f64(const StepArgs<double>& a, const RowMaps& maps, int order, int lim,
+                            bool vec, int grid, size_t smem, cudaStream_t s);
 // Several FP32 lattices in one launch (same scheme, limiter and column path).
 cudaError_t launch_step_batch_f32(const BatchArgs<float>& b, int order, int lim, bool vec,
                                   int grid, size_t smem, cudaStream_t s);

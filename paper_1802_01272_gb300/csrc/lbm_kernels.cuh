@@ -32,6 +32,7 @@
 // f^n (halo columns of neighbouring strips are L2 hits) and written once.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (type only)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -45,7 +46,8 @@ constexpr int NT = 16 * NG;     // threads per CTA
 constexpr int RPI = 4;          // rows per pipeline iteration
 constexpr int SG = NG + 2;      // staging groups per plane row: region plus one group per side
 constexpr int SCOL = 4 * SG;    // staging columns per plane row
-constexpr int SROWS = 2 * RPI + 1;  // staging ring rows (current window of RPI+1 rows + next RPI)
+constexpr int SROWS = 3 * RPI;  // staging ring rows: three batches of RPI rows (the batch read,
+                                // the last row of the one before, the batch being loaded)
 constexpr int FROWS = 8;        // advected-row ring (power of two)
 constexpr int MROWS = 8;        // moment rings (power of two)
 constexpr int WARMUP = 5;       // pipeline rows before the first output row of a segment
@@ -87,10 +89,17 @@ struct StepArgs {
   int walls, reservoir, regularize;
   T rho_ref, Tt, a, b, kappa, inv_ds, inv_ds2, dt, omega, one_m_omega, om2, om6;
   T rho_ext, rbc2, cxc, cyc;
-  unsigned int* err;
+  unsigned int* err;         // bit 0: non-finite or non-positive rho; bit 1: a wait timed out
+  int tma_ok;               // the launch's tensor map describes fin (interior strips use it)
   T xlo, xhi;               // |xi| components sqrt(3 - sqrt 6), sqrt(3 + sqrt 6)
   ClassConst<T> cls[4];     // groups (lo,lo), (hi,lo), (lo,hi), (hi,hi)
   VelConst<T> v[16];
+};
+
+// f^n as a 3-D tensor (x, plane, row) for tensor copies of staged rows:
+// m[0] copies boxes of SCOL columns x 16 planes x RPI rows, m[1] single rows.
+struct RowMaps {
+  CUtensorMap m[2];
 };
 
 constexpr int MAXB = 16;  // lattices per batched launch (kernel parameter space)

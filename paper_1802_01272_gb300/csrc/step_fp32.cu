@@ -19,12 +19,12 @@ void* select(int order, int lim, bool vec) {
 }
 }  // namespace
 
-cudaError_t launch_step_f32(const StepArgs<float>& a, int order, int lim, bool vec, int grid,
-                            size_t smem, cudaStream_t s) {
+cudaError_t launch_step_f32(const StepArgs<float>& a, const RowMaps& maps, int order, int lim,
+                            bool vec, int grid, size_t smem, cudaStream_t s) {
   void* fn = select(order, lim, vec);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  void* args[] = {const_cast<StepArgs<float>*>(&a)};
+  void* args[] = {const_cast<StepArgs<float>*>(&a), const_cast<RowMaps*>(&maps)};
   return cudaLaunchKernel(fn, dim3(grid), dim3(NT), args, smem, s);
 }
 

@@ -14,6 +14,62 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// ------------------------------------------- TMA row loads and mbarriers
+// Interior strips stage whole rows with one tensor copy per row: a box of
+// SCOL columns x 1 row x 16 planes of f^n lands as [16][SCOL] in the ring slot,
+// the same layout the per-thread copies produce.  Completion is counted in
+// bytes on an mbarrier; every wait is bounded in time.
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase `parity` of `bar` to complete, for at most ~1 s; false on
+// timeout (the caller records the error and stops waiting).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > 1000000000ULL) return false;
+  }
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// One tensor copy of rows y.. of the (x, plane, row) tensor: the box's rows
+// land as consecutive [16][SCOL] ring slots.
+__device__ __forceinline__ void tma_load_rows(void* dst, const CUtensorMap* map, int x, int y,
+                                              unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(0), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ int mod_pos(int a, int n) {  // a mod n for a > -n*1024
   return (a + n * 1024) % n;
 }
@@ -32,7 +88,11 @@ struct Smem {
   int* col;   // [SG] wrapped global column of each staging group
   double* dmass;              // fused diagnostics: per-CTA accumulators
   unsigned long long* dsums;  // [6]
+  unsigned long long* bar;    // [2] mbarriers of the tensor-copy batches (even, odd)
+  int* abort;                 // a bounded wait of this CTA timed out: stop waiting
   __device__ Smem(unsigned char* raw) {
+    // the ring starts on 128 bytes (tensor copies); the allocation has the slack
+    raw += (128u - ((unsigned)__cvta_generic_to_shared(raw) & 127u)) & 127u;
     T* p = reinterpret_cast<T*>(raw);
     stage = p;
     p += SROWS * 16 * SCOL;
@@ -47,6 +107,8 @@ struct Smem {
     col = reinterpret_cast<int*>(lap + MROWS * REG);
     dmass = reinterpret_cast<double*>(col + SG + (SG & 1));  // 8-byte aligned after 18 ints
     dsums = reinterpret_cast<unsigned long long*>(dmass + 1);
+    bar = dsums + 6;
+    abort = reinterpret_cast<int*>(bar + 2);
   }
 };
 
@@ -83,10 +145,11 @@ struct StageSlots {
 // (constant per plane) or wrap periodically.
 template <typename T, bool VEC>
 __device__ __forceinline__ void stage_rows(const StepArgs<T>& P, const Smem<T>& S,
-                                           const StageSlots<T>& sl, int r_begin, int r_end) {
+                                           const StageSlots<T>& sl, int r_begin, int r_end,
+                                           int rbase) {
   using SS = StageSlots<T>;
   for (int r = r_begin; r < r_end; ++r) {
-    T* srow = S.stage + mod_pos(r, SROWS) * 16 * SCOL;
+    T* srow = S.stage + mod_pos(r - rbase, SROWS) * 16 * SCOL;
     if (P.walls && (r < 0 || r >= P.Ly)) {
 #pragma unroll
       for (int m = 0; m < SS::NS; ++m) {
@@ -121,14 +184,88 @@ __device__ __forceinline__ void stage_rows(const StepArgs<T>& P, const Smem<T>& 
   }
 }
 
+// Tensor-copy staging of rows [r_begin, r_end) for a strip whose staging
+// columns [x0, x0 + SCOL) lie inside the lattice.  Ring slot of row r:
+// (r - rbase) mod SROWS, so every batch of RPI rows starting at rbase + RPI i
+// fills RPI consecutive slots and, away from the lattice's y ends, is ONE copy
+// through the RPI-row map; rows that wrap periodically or sit next to a wall go
+// one per copy through the 1-row map.  Thread 0 arms the batch's mbarrier with
+// the byte count first; wall ghost rows (constant per plane) are written by
+// all threads.  `fence` orders earlier generic writes of the ring (ghost rows)
+// before the copies.
+template <typename T>
+__device__ __forceinline__ void stage_rows_tma(const StepArgs<T>& P, const Smem<T>& S,
+                                               const StageSlots<T>& sl, const CUtensorMap* tm,
+                                               int x0, int r_begin, int r_end, int rbase,
+                                               unsigned batch, bool fence) {
+  using SS = StageSlots<T>;
+  constexpr unsigned ROW_BYTES = 16u * SCOL * (unsigned)sizeof(T);
+  const int Ly = P.Ly;
+  if (threadIdx.x == 0) {
+    unsigned long long* bar = S.bar + (batch & 1u);
+    if (fence) fence_proxy_async();
+    if (r_end - r_begin == RPI && r_begin >= 0 && r_end <= Ly &&
+        mod_pos(r_begin - rbase, RPI) == 0) {
+      mbar_arrive_expect_tx(bar, RPI * ROW_BYTES);
+      tma_load_rows(S.stage + mod_pos(r_begin - rbase, SROWS) * 16 * SCOL, tm, x0, r_begin, bar);
+    } else {
+      unsigned bytes = 0;
+      for (int r = r_begin; r < r_end; ++r)
+        if (!(P.walls && (r < 0 || r >= Ly))) bytes += ROW_BYTES;
+      mbar_arrive_expect_tx(bar, bytes);
+      for (int r = r_begin; r < r_end;) {
+        T* dst = S.stage + mod_pos(r - rbase, SROWS) * 16 * SCOL;
+        if (mod_pos(r - rbase, RPI) == 0 && r + RPI <= r_end && r >= 0 && r + RPI <= Ly) {
+          tma_load_rows(dst, tm, x0, r, bar);  // an aligned batch inside the lattice
+          r += RPI;
+          continue;
+        }
+        if (!(P.walls && (r < 0 || r >= Ly))) {
+          int rw = r % Ly;
+          if (rw < 0) rw += Ly;
+          tma_load_rows(dst, tm + 1, x0, rw, bar);
+        }
+        ++r;
+      }
+    }
+  }
+  if (P.walls && (r_begin < 0 || r_end > Ly)) {
+    for (int r = r_begin; r < r_end; ++r) {
+      if (r >= 0 && r < Ly) continue;
+      T* srow = S.stage + mod_pos(r - rbase, SROWS) * 16 * SCOL;
+#pragma unroll
+      for (int m = 0; m < SS::NS; ++m) {
+        const int c = threadIdx.x + NT * m;
+        if (c < SS::PER_ROW) {
+          const T gv = r < 0 ? P.v[c / SS::CH].gbot : P.v[c / SS::CH].gtop;
+#pragma unroll
+          for (int e = 0; e < SS::EPC; ++e) srow[sl.dst[m] + e] = gv;
+        }
+      }
+    }
+  }
+}
+
+// Every thread waits for tensor-copy batch `batch` (bounded); a timeout sets
+// the step's error bit 2 and the CTA stops waiting (its results are void).
+template <typename T>
+__device__ __forceinline__ void tma_wait_batch(const StepArgs<T>& P, const Smem<T>& S,
+                                               unsigned batch) {
+  if (*reinterpret_cast<volatile int*>(S.abort)) return;
+  if (!mbar_wait_bounded(S.bar + (batch & 1u), (batch >> 1) & 1u)) {
+    *reinterpret_cast<volatile int*>(S.abort) = 1;
+    atomicOr(P.err, 2u);
+  }
+}
+
 // P1 for one warp quadrant: rows a0 .. a0+RPI-1 of plane k, two rows per loop
 // trip so that the two-row history rotates by register renaming.
 template <int SX, int SY, int ORDER, int LIM, typename T>
 __device__ __forceinline__ void advect_rows(const StepArgs<T>& P, const Smem<T>& S,
                                             AdvState<T>& st, const VelConst<T>& vc, int a0,
-                                            int src_off, int dst_off, bool ghosts) {
+                                            int rbase, int src_off, int dst_off, bool ghosts) {
   constexpr int LAG = SY > 0 ? 1 : 2;  // staged row read for output row a
-  int slot = mod_pos(a0 + LAG, SROWS);
+  int slot = mod_pos(a0 + LAG - rbase, SROWS);
 #pragma unroll 1
   for (int j = 0; j < RPI; j += 2) {
 #pragma unroll
@@ -163,7 +300,8 @@ __device__ __forceinline__ void advect_rows(const StepArgs<T>& P, const Smem<T>&
 // so results do not depend on how the rows are split over CTAs or lattices.
 template <typename T, int ORDER, int LIM, bool VEC>
 __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T>& S, int strip,
-                                            int ys, int ye) {
+                                            int ys, int ye, const CUtensorMap* tm,
+                                            unsigned& batch) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   // P1 layout: a warp = one sign quadrant x two velocity groups x 16 column
@@ -197,16 +335,34 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T>&
     const bool p4_col_ok = p4_col < XOFF + TW && p4_x < Lx;
 
     const StageSlots<T> slots(P, S, VEC);
+    // interior strips stage by tensor copies, the strips at the periodic x
+    // seam (and lattices without a tensor map) by per-thread copies
+    const int x0 = strip * TW - XOFF - 4;
+    const bool tma = VEC && tm != nullptr && x0 >= 0 && x0 + SCOL <= Lx;
+    // ghost rows are written by threads into slots the copies reuse later
+    const bool fence = P.walls && (ys < 2 * SROWS || ye + 2 * SROWS > Ly);
     int a0 = ys - WARMUP;
-    stage_rows<T, VEC>(P, S, slots, a0 + 1, a0 + RPI + 2);
+    const int rbase = a0 + 2;  // first row of every iteration's batch: rbase + RPI i
+    if (tma)
+      stage_rows_tma<T>(P, S, slots, tm, x0, a0 + 1, a0 + RPI + 2, rbase, batch, fence);
+    else
+      stage_rows<T, VEC>(P, S, slots, a0 + 1, a0 + RPI + 2, rbase);
     cp_async_commit();
 
     for (; a0 - 2 < ye; a0 += RPI) {
       // ---------------- L: prefetch the rows only the next iteration needs
       const bool more = (a0 + RPI) - 2 < ye;
-      if (more) stage_rows<T, VEC>(P, S, slots, a0 + RPI + 2, a0 + 2 * RPI + 2);
-      cp_async_commit();
-      cp_async_wait<1>();
+      if (tma) {
+        if (more)
+          stage_rows_tma<T>(P, S, slots, tm, x0, a0 + RPI + 2, a0 + 2 * RPI + 2, rbase, batch + 1,
+                            fence);
+        tma_wait_batch<T>(P, S, batch);
+        ++batch;
+      } else {
+        if (more) stage_rows<T, VEC>(P, S, slots, a0 + RPI + 2, a0 + 2 * RPI + 2, rbase);
+        cp_async_commit();
+        cp_async_wait<1>();
+      }
       __syncthreads();
 
       // ---------------- P1: advect rows a0 .. a0+RPI-1 of plane k
@@ -214,10 +370,10 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T>&
         const bool ghosts = P.walls && (a0 < 0 || a0 + RPI > Ly);  // any wall ghost row here
         const int so = k * SCOL + 4 * g, dof = k * REG + 4 * g;
         switch (q) {
-          case 0: advect_rows<+1, +1, ORDER, LIM>(P, S, st, vc, a0, so, dof, ghosts); break;
-          case 1: advect_rows<-1, +1, ORDER, LIM>(P, S, st, vc, a0, so, dof, ghosts); break;
-          case 2: advect_rows<-1, -1, ORDER, LIM>(P, S, st, vc, a0, so, dof, ghosts); break;
-          default: advect_rows<+1, -1, ORDER, LIM>(P, S, st, vc, a0, so, dof, ghosts); break;
+          case 0: advect_rows<+1, +1, ORDER, LIM>(P, S, st, vc, a0, rbase, so, dof, ghosts); break;
+          case 1: advect_rows<-1, +1, ORDER, LIM>(P, S, st, vc, a0, rbase, so, dof, ghosts); break;
+          case 2: advect_rows<-1, -1, ORDER, LIM>(P, S, st, vc, a0, rbase, so, dof, ghosts); break;
+          default: advect_rows<+1, -1, ORDER, LIM>(P, S, st, vc, a0, rbase, so, dof, ghosts); break;
         }
       }
       __syncthreads();
@@ -384,10 +540,12 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T>&
         if (P.diag_mass) {  // fused diagnostics: warp sums, then per-CTA shared accumulators
           const bool on = rho_post >= T(0);
           const bool in = on && rho_post < P.diag_thr;
-          double m = on ? (double)rho_post : 0.0;
+          // warp sum in the storage precision (GB300's FP64 issue rate is
+          // low), accumulated per CTA in FP64
+          T m = on ? rho_post : T(0);
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) m += __shfl_down_sync(0xffffffffu, m, o);
-          if (lane == 0) atomicAdd(S.dmass, m);
+          if (lane == 0) atomicAdd(S.dmass, (double)m);
           if (__ballot_sync(0xffffffffu, in)) {  // bubble sites are rare: sum them only here
             const unsigned long long i = in ? (unsigned long long)p4_x : 0ULL;
             const unsigned long long j = in ? (unsigned long long)c : 0ULL;
@@ -432,14 +590,20 @@ __device__ __forceinline__ void retire_cta(unsigned long long* sched) {
 
 template <typename T, int ORDER, int LIM, bool VEC>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
-    step_kernel(const __grid_constant__ StepArgs<T> P) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+    step_kernel(const __grid_constant__ StepArgs<T> P, const __grid_constant__ RowMaps maps) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const Smem<T> S(smem_raw);
   __shared__ long long s_item;
   if (threadIdx.x == 0) {
     *S.dmass = 0.0;
     for (int t = 0; t < 6; ++t) S.dsums[t] = 0ULL;
+    *S.abort = 0;
+    mbar_init(S.bar, 1);
+    mbar_init(S.bar + 1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
+  const CUtensorMap* tm = P.tma_ok ? maps.m : nullptr;
+  unsigned batch = 0;  // tensor-copy batches issued (and consumed) by this CTA
   for (;;) {
     const long long item = claim_item(P.sched, &s_item);
     if (item >= P.items) break;
@@ -447,7 +611,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     const int strip = (int)(item - rb * P.nstrip);
     const int ys = (int)(rb * P.row_block);
     const int ye = min(P.Ly, ys + P.row_block);
-    run_segment<T, ORDER, LIM, VEC>(P, S, strip, ys, ye);
+    run_segment<T, ORDER, LIM, VEC>(P, S, strip, ys, ye, tm, batch);
   }
   // claim_item's barrier after the last claim orders every warp's shared adds
   if (P.diag_mass && threadIdx.x == 0) {
@@ -462,10 +626,11 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
 template <typename T, int ORDER, int LIM, bool VEC>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     step_batch_kernel(const __grid_constant__ BatchArgs<T> B) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const Smem<T> S(smem_raw);
   __shared__ long long s_item;
   int i = 0;
+  unsigned batch = 0;  // unused: batched lattices stage by per-thread copies
   for (;;) {
     const long long item = claim_item(B.sched, &s_item);
     if (item >= B.item_start[B.count]) break;
@@ -476,7 +641,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     const int strip = (int)(local - rb * P.nstrip);
     const int ys = (int)(rb * P.row_block);
     const int ye = min(P.Ly, ys + P.row_block);
-    run_segment<T, ORDER, LIM, VEC>(P, S, strip, ys, ye);
+    run_segment<T, ORDER, LIM, VEC>(P, S, strip, ys, ye, nullptr, batch);
   }
   retire_cta(B.sched);
 }

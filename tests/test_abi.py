@@ -40,11 +40,12 @@ def test_every_declared_symbol_is_exported(P):
 
 
 def test_struct_layout_matches_header(P, tmp_path):
-    from paper_1802_01272_gb300.binding import lbm_diag, lbm_params
+    from paper_1802_01272_gb300.binding import lbm_diag, lbm_kernel_info, lbm_params
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "ctulbm.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(lbm_params),'
-                   ' sizeof(lbm_diag), offsetof(lbm_params, rho_ref), offsetof(lbm_diag, theta));'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(lbm_params),'
+                   ' sizeof(lbm_diag), offsetof(lbm_params, rho_ref), offsetof(lbm_diag, theta),'
+                   ' sizeof(lbm_kernel_info), offsetof(lbm_kernel_info, tensor_copies));'
                    'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
@@ -52,7 +53,8 @@ def test_struct_layout_matches_header(P, tmp_path):
     vals = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True,
                                         check=True).stdout.split()))
     assert vals == [C.sizeof(lbm_params), C.sizeof(lbm_diag), lbm_params.rho_ref.offset,
-                    lbm_diag.theta.offset]
+                    lbm_diag.theta.offset, C.sizeof(lbm_kernel_info),
+                    lbm_kernel_info.tensor_copies.offset]
 
 
 def test_defaults_are_the_papers(P):

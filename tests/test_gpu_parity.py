@@ -75,6 +75,10 @@ CASES = [
     (300, 300, 2, 0, 0, 1, 0),     # reservoir (R_BC = 22 nodes at ds = 1/256)
     (60, 44, 2, 0, 0, 0, 1),       # regularisation
     (60, 44, 2, 0, 1, 0, 1),
+    # interior strips staged by tensor copies; Ly not a multiple of the 4-row
+    # batches, several row blocks (96 rows each) of a work item
+    (240, 150, 2, 0, 0, 0, 0),
+    (240, 200, 2, 0, 1, 0, 0),
 ]
 
 
@@ -93,6 +97,19 @@ def test_variants_fp64(P, oracle_mod, case):
     f0 = O.init_feq(op, rho, ux, uy)
     for n, fg, fo, L in run_both(P, O, lp, f0, [1, 7]):
         assert rel_err(fg, fo) < TOL64, f"after {n} steps"
+
+
+def test_kernel_info_staging_paths(P):
+    """Lattices with Lx a multiple of 4 and at least 72 wide stage their
+    interior strips with tensor copies; others use per-thread copies only."""
+    for (Lx, Ly, prec, want) in ((240, 200, P.LBM_FP64, 1), (240, 200, P.LBM_FP32_SHIFTED, 1),
+                                 (6144, 64, P.LBM_FP32_SHIFTED, 1), (37, 23, P.LBM_FP64, 0),
+                                 (64, 48, P.LBM_FP32_SHIFTED, 0)):
+        with P.Lattice(P.Params(Lx=Lx, Ly=Ly, precision=prec)) as L:
+            k = L.kernel_info()
+        assert k["tensor_copies"] == want, (Lx, Ly, prec, k)
+        assert k["threads"] == 256 and k["strips"] == (Lx + 55) // 56 and k["grid"] >= 1
+        assert 96 <= k["row_block"] <= 256
 
 
 def test_fp32_shifted_1000_steps(P, oracle_mod):

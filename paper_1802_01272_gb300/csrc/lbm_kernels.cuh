@@ -127,7 +127,14 @@ __device__ __forceinline__ float min3(float a, float b, float c) {
   return r;
 }
 __device__ __forceinline__ double min3(double a, double b, double c) { return fmin(fmin(a, b), c); }
-__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+// Reciprocal in FP32: the hardware approximation (relative error below 2^-22),
+// enough for u = (rho u)/rho and the pressure and force terms, which enter the
+// update multiplied by dt; FP64 keeps the correctly rounded division.
+__device__ __forceinline__ float rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 
 // Half of the limited jump R * Psi(Ru / R) of Sec. II C 2.  For the MC limiter,

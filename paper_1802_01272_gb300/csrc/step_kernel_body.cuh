@@ -519,20 +519,31 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T>&
             const T P0 = p0 + cl.omA, P1 = p1 + cl.Ak, K1c = p2 + cl.omB, wr = cl.w * rho;
             const T sw = scale * wr, radd = cl.w * add;
             const T s1 = scale * P.one_m_omega;
+            // opposite velocities (sign patterns s and s + 2) differ only in
+            // the sign of xi.u and xi.g: split the cubic into its even and odd
+            // parts E and O, so that poly(+) = E + O and poly(-) = E - O
+            T outv[4];
 #pragma unroll
-            for (int sgn = 0; sgn < 4; ++sgn) {
+            for (int sgn = 0; sgn < 2; ++sgn) {
               const int kk = 4 * grp + sgn;
-              const bool nx = sgn == 1 || sgn == 2, ny = sgn >= 2;
-              const T cu = (nx ? -mxu[ix] : mxu[ix]) + (ny ? -myu[iy] : myu[iy]);   // xi.u
-              const T D = (nx ? -mxg[ix] : mxg[ix]) + (ny ? -myg[iy] : myg[iy]);    // dt xi.g
-              const T K0 = D * P1 + P0;
-              const T K1 = K1c + D;
-              const T K2 = T(0.5) * D + P.om2;
-              // (omega f^eq + dt F_k - omega w rho_ref) / (w rho): a cubic in xi.u
-              const T poly = K0 + cu * (K1 + cu * (K2 + cu * P.om6));
+              const bool nx = sgn == 1;
+              const T cu = (nx ? -mxu[ix] : mxu[ix]) + myu[iy];  // xi.u
+              const T D = (nx ? -mxg[ix] : mxg[ix]) + myg[iy];   // dt xi.g
+              // poly = K0 + cu (K1 + cu (K2 + cu om/6)) with K0 = D P1 + P0,
+              // K1 = K1c + D, K2 = D/2 + om/2: the cubic in xi.u of
+              // (omega f^eq + dt F_k - omega w rho_ref) / (w rho)
+              const T c2 = cu * cu;
+              const T E = c2 * P.om2 + (cu * D + P0);
+              const T O = cu * (c2 * P.om6 + K1c) + D * (c2 * T(0.5) + P1);
               // f^{n+1} = (1 - omega) f* + w rho poly, then the reservoir rescale
               // s f + w rho_ref (s - 1) outside R_BC (s = 1, add = 0 elsewhere)
-              *dst = s1 * base[kk] + (sw * poly + radd);
+              const T Q = sw * E + radd;
+              outv[sgn] = s1 * base[kk] + (sw * O + Q);
+              outv[sgn + 2] = s1 * base[kk + 2] + (Q - sw * O);
+            }
+#pragma unroll
+            for (int sgn = 0; sgn < 4; ++sgn) {
+              *dst = outv[sgn];
               dst += pl;
             }
           }

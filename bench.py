@@ -36,6 +36,9 @@ WORKLOADS = {
     # the same physics on a 2048^2 lattice (2 x 268 MB), small enough for ncu captures
     "sheared-bubble-2048": dict(L=2048, T=0.8, tau=1e-2, rho_ext=1.90, rho_v=0.23967, R=26.0,
                                 W=4.0, shear_dt=5e-6, walls=True, precision="fp32"),
+    # FP16 shifted storage of the same workload: half the bytes per node update
+    "sheared-bubble-6144-fp16": dict(L=6144, T=0.8, tau=1e-2, rho_ext=1.90, rho_v=0.23967, R=26.0,
+                                     W=4.0, shear_dt=5e-6, walls=True, precision="fp16"),
     "quiescent-bubble-4096": dict(L=4096, T=0.9, tau=1e-3, rho_ext=1.58, rho_v=0.425742, R=20.0,
                                   W=4.0, shear_dt=0.0, walls=False, precision="fp32",
                                   reservoir=True),
@@ -49,7 +52,8 @@ DT, DS = 1e-4, 1.0 / 256.0
 def lib_params(P, w):
     L = w["L"]
     p = P.Params(Lx=L, Ly=L, T=w["T"], tau=w["tau"], dt=DT, ds=DS, rho_ext=w["rho_ext"],
-                 precision=P.LBM_FP32_SHIFTED if w["precision"] == "fp32" else P.LBM_FP64,
+                 precision={"fp32": P.LBM_FP32_SHIFTED, "fp16": P.LBM_FP16_SHIFTED,
+                            "fp64": P.LBM_FP64}[w["precision"]],
                  rho_ref=w["rho_ext"])
     if w["walls"]:
         p.boundary = P.LBM_BC_SHEAR_WALLS
@@ -79,7 +83,8 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = ("lbm_kernels.cuh", "step_kernel_body.cuh", "step_fp32.cu", "step_fp64.cu")
+KERNEL_SOURCES = ("lbm_kernels.cuh", "step_kernel_body.cuh", "step_fp32.cu", "step_fp64.cu",
+                  "step_fp16.cu")
 
 
 def kernel_source_hash():
@@ -291,7 +296,7 @@ def main():
         p.limiter = args.limiter
     rho, ux, uy = initial_fields(w, p.Lx, p.Ly)
     nodes = p.Lx * p.Ly
-    elem = 4 if p.precision == P.LBM_FP32_SHIFTED else 8
+    elem = {P.LBM_FP32_SHIFTED: 4, P.LBM_FP16_SHIFTED: 2}.get(p.precision, 8)
 
     def barrier():
         torch.cuda.synchronize()
@@ -378,9 +383,10 @@ def main():
             "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if elem == 4 else "f64", "data": "synthetic",
+            "dtype": "f64" if elem == 8 else "f32", "data": "synthetic",
             "config": {"workload": args.workload, "lattice": [p.Lx, p.Ly],
-                       "storage": "fp32 shifted (f - w rho_ref)" if elem == 4 else "fp64",
+                       "storage": {4: "fp32 shifted (f - w rho_ref)",
+                                   2: "fp16 shifted (f - w rho_ref), fp32 arithmetic"}.get(elem, "fp64"),
                        "scheme": {1: "CTU1", 2: "CTU2"}[p.ctu_order] +
                                  {0: " + MC limiter", 1: " (Psi = 0)", 2: " (Psi = 1)"}[p.limiter]
                                  if p.ctu_order == 2 else "CTU1", "T": p.T, "tau": p.tau,

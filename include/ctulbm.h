@@ -65,13 +65,19 @@ extern "C" {
 #define LBM_BC_SHEAR_WALLS 1       /* Sec. III C */
 #define LBM_FP64 0                 /* f stored and computed in FP64 */
 #define LBM_FP32_SHIFTED 1         /* f - w_k rho_ref stored and computed in FP32 */
+#define LBM_FP16_SHIFTED 2         /* f - w_k rho_ref stored in FP16 (IEEE half), computed
+                                      in FP32: half the memory traffic of FP32 storage,
+                                      ~5e-4 relative rounding of the stored deviations per
+                                      step (no counterpart in the paper, which computes in
+                                      double precision) */
 
 /* ---- parameters -------------------------------------------------------------
  * Defaults (lbm_default_params): a = 9/8, b = 1/3, kappa = 1e-4, T = 0.9,
  * tau = 1e-3, dt = 1e-4, ds = 1/256, CTU2 with the MC limiter, periodic,
  * FP32_SHIFTED with rho_ref = 1 (Sec. II D-E and III A).                   */
 typedef struct lbm_params {
-  int32_t Lx, Ly;          /* lattice nodes, each >= 1; FP32 storage with Lx % 4 == 0 is the fast path */
+  int32_t Lx, Ly;          /* lattice nodes, each >= 1; the fast path wants Lx % 4 == 0
+                              (Lx % 8 == 0 for FP16 storage) and Lx >= 72 */
   int32_t velset;          /* LBM_VEL_D2Q16_H3 */
   double a, b, kappa, T;   /* p^w = rho T/(1 - b rho) - a rho^2 (Eq. evdw); kappa of Eq. eder; T/T_c */
   double tau, dt, ds;      /* relaxation time, time step, lattice spacing */
@@ -83,8 +89,8 @@ typedef struct lbm_params {
   double rho_ext;          /* density of the wall ghost rows and of the reservoir */
   int32_t reservoir;       /* 0 or 1: after every step, f <- f rho_ext/rho outside
                               R_BC = min(Lx,Ly)/2 - 1/(2 ds) nodes from (Lx/2, Ly/2) */
-  int32_t precision;       /* LBM_FP64 | LBM_FP32_SHIFTED */
-  double rho_ref;          /* shift of the FP32 storage (ignored in FP64) */
+  int32_t precision;       /* LBM_FP64 | LBM_FP32_SHIFTED | LBM_FP16_SHIFTED */
+  double rho_ref;          /* shift of the FP32 / FP16 storage (ignored in FP64) */
 } lbm_params;
 
 /* Diagnostics record (Sec. III B-C).  Bubble sites are nodes with
@@ -174,7 +180,8 @@ int lbm_histogram(lbm_handle* h, int32_t nbins, double lo, double hi, int64_t* c
  * their own buffers with no lbm_handle.  (lbm_histogram allocates a device
  * counts buffer on every call.)
  *   f_device : device pointer, [16][Ly][Lx], FP64 f when precision is LBM_FP64,
- *              float (f - w_k rho_ref) when it is LBM_FP32_SHIFTED
+ *              float (f - w_k rho_ref) when it is LBM_FP32_SHIFTED, IEEE half
+ *              (f - w_k rho_ref) when it is LBM_FP16_SHIFTED
  *   nbins    : 1 .. LBM_NOALLOC_MAX_BINS; more returns LBM_ERR_INVALID_ARG
  *   counts   : host array of nbins int64, filled before return (the call
  *              synchronises cuda_stream); bins as in lbm_histogram

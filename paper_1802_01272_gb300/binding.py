@@ -17,7 +17,7 @@ from . import build as _build
 LBM_VEL_D2Q16_H3 = 0
 LBM_LIM_MC, LBM_LIM_ZERO, LBM_LIM_ONE = 0, 1, 2
 LBM_BC_PERIODIC, LBM_BC_SHEAR_WALLS = 0, 1
-LBM_FP64, LBM_FP32_SHIFTED = 0, 1
+LBM_FP64, LBM_FP32_SHIFTED, LBM_FP16_SHIFTED = 0, 1, 2
 
 ERRORS = {
     -1: "LBM_ERR_INVALID_ARG", -2: "LBM_ERR_CFL", -3: "LBM_ERR_DENSITY_RANGE",
@@ -191,10 +191,11 @@ NOALLOC_MAX_BINS = 4096
 def histogram_noalloc(f, precision: int, rho_ref: float, nbins: int, lo: float, hi: float,
                       stream=None) -> np.ndarray:
     """lbm_histogram_noalloc on a caller-owned torch CUDA tensor f of shape
-    [16, Ly, Lx] (float64 for LBM_FP64, float32 shifted for LBM_FP32_SHIFTED).
-    Allocates no device memory; see include/ctulbm.h for the shared-array rules."""
+    [16, Ly, Lx] (float64 for LBM_FP64, shifted float32 / float16 for
+    LBM_FP32_SHIFTED / LBM_FP16_SHIFTED).  Allocates no device memory; see
+    include/ctulbm.h for the shared-array rules."""
     import torch
-    want = torch.float64 if precision == LBM_FP64 else torch.float32
+    want = {LBM_FP64: torch.float64, LBM_FP16_SHIFTED: torch.float16}.get(precision, torch.float32)
     if not (isinstance(f, torch.Tensor) and f.is_cuda and f.dtype == want and f.is_contiguous()
             and f.dim() == 3 and f.shape[0] == 16):
         raise ValueError(f"expected a contiguous {want} CUDA tensor of shape [16, Ly, Lx]")

@@ -101,7 +101,10 @@ bool encode_row_map(void* base, size_t elem, int Lx, int Ly, int rows, CUtensorM
   const cuuint64_t strides[2] = {(cuuint64_t)Lx * (cuuint64_t)Ly * elem, (cuuint64_t)Lx * elem};
   const cuuint32_t box[3] = {(cuuint32_t)SCOL, 16, (cuuint32_t)rows};
   const cuuint32_t estr[3] = {1, 1, 1};
-  return enc(out, elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+  const CUtensorMapDataType type = elem == 8   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                   : elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  return enc(out, type, 3,
              base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -233,7 +236,9 @@ int validate(const lbm_params* p) {
   if (p->limiter < 0 || p->limiter > 2) return LBM_ERR_INVALID_ARG;
   if (p->boundary != LBM_BC_PERIODIC && p->boundary != LBM_BC_SHEAR_WALLS)
     return LBM_ERR_INVALID_ARG;
-  if (p->precision != LBM_FP64 && p->precision != LBM_FP32_SHIFTED) return LBM_ERR_UNSUPPORTED;
+  if (p->precision != LBM_FP64 && p->precision != LBM_FP32_SHIFTED &&
+      p->precision != LBM_FP16_SHIFTED)
+    return LBM_ERR_UNSUPPORTED;
   if (p->regularize != 0 && p->regularize != 1) return LBM_ERR_INVALID_ARG;
   if (p->reservoir != 0 && p->reservoir != 1) return LBM_ERR_INVALID_ARG;
   if (!(p->tau > 0) || !(p->dt > 0) || !(p->ds > 0) || !(p->T > 0)) return LBM_ERR_INVALID_ARG;
@@ -245,7 +250,7 @@ int validate(const lbm_params* p) {
     if (!(p->rho_ext > 0) || (p->b > 0 && !(p->rho_ext * p->b < 1.0))) return LBM_ERR_DENSITY_RANGE;
   }
   if (!std::isfinite(p->shear_rate)) return LBM_ERR_INVALID_ARG;
-  if (p->precision == LBM_FP32_SHIFTED && !std::isfinite(p->rho_ref)) return LBM_ERR_INVALID_ARG;
+  if (p->precision != LBM_FP64 && !std::isfinite(p->rho_ref)) return LBM_ERR_INVALID_ARG;
   return LBM_OK;
 }
 
@@ -343,7 +348,7 @@ int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out) {
     delete h;
     return LBM_ERR_CUDA;
   }
-  h->elem = p->precision == LBM_FP64 ? 8 : 4;
+  h->elem = p->precision == LBM_FP64 ? 8 : (p->precision == LBM_FP16_SHIFTED ? 2 : 4);
   velocity_table(h->xi, h->w);
   const size_t plane = (size_t)p->Lx * p->Ly;
   const size_t bytes = 16 * plane * h->elem;
@@ -363,11 +368,13 @@ int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out) {
   // launch geometry: strips of TW output columns, rows split evenly over a
   // persistent grid of (SMs x resident CTAs), at least 48 rows per CTA
   h->nstrip = (p->Lx + TW - 1) / TW;
-  h->vec = (p->Lx % 4) == 0;
-  h->smem = step_smem_bytes(h->elem);
+  // 16-byte copies of staging groups: 4 columns (float, double) or 8 (half)
+  h->vec = (p->Lx % (h->elem == 2 ? 8 : 4)) == 0;
+  h->smem = step_smem_bytes(h->elem, h->elem == 8 ? 8 : 4);
   const int lim = p->ctu_order == 1 ? 0 : p->limiter;
-  int occ = h->elem == 4 ? step_occupancy_f32(p->ctu_order, lim, h->vec, h->smem)
-                         : step_occupancy_f64(p->ctu_order, lim, h->vec, h->smem);
+  int occ = h->elem == 4   ? step_occupancy_f32(p->ctu_order, lim, h->vec, h->smem)
+            : h->elem == 2 ? step_occupancy_f16(p->ctu_order, lim, h->vec, h->smem)
+                           : step_occupancy_f64(p->ctu_order, lim, h->vec, h->smem);
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
   if (occ < 1 || nsm < 1) {
@@ -385,10 +392,10 @@ int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out) {
   const long long items = (long long)((p->Ly + rb - 1) / rb) * h->nstrip;
   h->grid = (int)(items < grid_max ? items : grid_max);
   h->rows_per_cta = 0;
-  if (h->elem == 4)
-    fill_step_args<float>(h, h->a32);
-  else
+  if (h->elem == 8)
     fill_step_args<double>(h, h->a64);
+  else
+    fill_step_args<float>(h, h->a32);
   std::memset(h->tmap, 0, sizeof(h->tmap));
   bool tma = h->vec;
   for (int i = 0; i < 2 && tma; ++i)
@@ -400,7 +407,7 @@ int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out) {
   x.Lx = p->Lx;
   x.Ly = p->Ly;
   x.plane = (long long)plane;
-  x.storage64 = h->elem == 8;
+  x.storage = h->elem == 8 ? STORE_F64 : (h->elem == 2 ? STORE_F16 : STORE_F32);
   x.rho_ref = rho_ref_of(*p);
   x.Tt = p->T;
   std::memcpy(x.xi, h->xi, sizeof(h->xi));
@@ -510,11 +517,12 @@ int lbm_step(lbm_handle* h, int64_t n) {
   const int lim = h->p.ctu_order == 1 ? 0 : h->p.limiter;
   for (int64_t s = 0; s < n; ++s) {
     cudaError_t e;
-    if (h->elem == 4) {
-      h->a32.fin = static_cast<const float*>(h->f[h->cur]);
-      h->a32.fout = static_cast<float*>(h->f[1 - h->cur]);
-      e = launch_step_f32(h->a32, h->tmap[h->cur], h->p.ctu_order, lim, h->vec, h->grid, h->smem,
-                          h->stream);
+    if (h->elem != 8) {
+      h->a32.fin = h->f[h->cur];
+      h->a32.fout = h->f[1 - h->cur];
+      e = (h->elem == 4 ? launch_step_f32 : launch_step_f16)(h->a32, h->tmap[h->cur],
+                                                             h->p.ctu_order, lim, h->vec, h->grid,
+                                                             h->smem, h->stream);
     } else {
       h->a64.fin = static_cast<const double*>(h->f[h->cur]);
       h->a64.fout = static_cast<double*>(h->f[1 - h->cur]);
@@ -611,15 +619,15 @@ int lbm_step_diag(lbm_handle* h, int64_t n, double threshold, lbm_diag* out) {
   if (cuda_check(h, cudaMemsetAsync(h->d_acc, 0, sizeof(DiagAcc), h->stream))) return h->sticky;
   const int lim = h->p.ctu_order == 1 ? 0 : h->p.limiter;
   cudaError_t e;
-  if (h->elem == 4) {
+  if (h->elem != 8) {
     StepArgs<float> a = h->a32;
-    a.fin = static_cast<const float*>(h->f[h->cur]);
-    a.fout = static_cast<float*>(h->f[1 - h->cur]);
+    a.fin = h->f[h->cur];
+    a.fout = h->f[1 - h->cur];
     a.diag_mass = &h->d_acc->mass;
     a.diag_sums = &h->d_acc->nb;
     a.diag_thr = (float)threshold;
-    e = launch_step_f32(a, h->tmap[h->cur], h->p.ctu_order, lim, h->vec, h->grid, h->smem,
-                        h->stream);
+    e = (h->elem == 4 ? launch_step_f32 : launch_step_f16)(a, h->tmap[h->cur], h->p.ctu_order, lim,
+                                                           h->vec, h->grid, h->smem, h->stream);
   } else {
     StepArgs<double> a = h->a64;
     a.fin = static_cast<const double*>(h->f[h->cur]);
@@ -712,7 +720,7 @@ int lbm_get_kernel_info(const lbm_handle* h, lbm_kernel_info* out) {
   out->smem_bytes = (int32_t)h->smem;
   out->strips = h->nstrip;
   out->row_block = h->row_block;
-  out->tensor_copies = h->elem == 4 ? h->a32.tma_ok : h->a64.tma_ok;
+  out->tensor_copies = h->elem == 8 ? h->a64.tma_ok : h->a32.tma_ok;
   return LBM_OK;
 }
 

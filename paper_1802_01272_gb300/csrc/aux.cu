@@ -2,6 +2,8 @@
 // (Eq. herfeq), FP64 <-> storage conversion, moments (Sec. II A) and the
 // diagnostics of Sec. III B-C (mass, bubble-site sums of Eq. gyr, probe
 // densities, density histogram).
+#include <type_traits>
+
 #include "lbm_internal.h"
 
 namespace ctulbm {
@@ -9,6 +11,16 @@ namespace ctulbm {
 namespace {
 
 constexpr int BS = 256;
+
+// Arithmetic type of a storage type: double for double, float for float and half.
+template <typename S>
+struct Comp {
+  using type = float;
+};
+template <>
+struct Comp<double> {
+  using type = double;
+};
 
 // Velocity table in the storage precision, loaded once per thread.
 template <typename T>
@@ -27,9 +39,10 @@ struct Vel {
 // Eq. (herfeq) with the storage shift w_k rho_ref removed:
 // f^eq - w rho_ref = w [ (rho - rho_ref) + rho (P_k - 1) ],
 // P_k - 1 = xi.u + [(xi.u)^2 - u^2 + (T-1)(xi^2-2)]/2 + xi.u [(xi.u)^2 - 3u^2 + 3(T-1)(xi^2-4)]/6
-template <typename T>
-__global__ void init_feq_kernel(const AuxArgs a, T* f, const double* rho, const double* ux,
+template <typename S>
+__global__ void init_feq_kernel(const AuxArgs a, S* f, const double* rho, const double* ux,
                                 const double* uy) {
+  using T = typename Comp<S>::type;
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= a.plane) return;
   const Vel<T> v(a);
@@ -40,40 +53,45 @@ __global__ void init_feq_kernel(const AuxArgs a, T* f, const double* rho, const 
     const T cu = v.x[k] * u + v.y[k] * w, x2 = v.x[k] * v.x[k] + v.y[k] * v.y[k];
     const T pm1 = cu + T(0.5) * (cu * cu - u2 + Tm1 * (x2 - T(2))) +
                   cu / T(6) * (cu * cu - T(3) * u2 + T(3) * Tm1 * (x2 - T(4)));
-    f[k * a.plane + q] = v.w[k] * (drho + r * pm1);
+    f[k * a.plane + q] = to_store<S, T>(v.w[k] * (drho + r * pm1));
   }
 }
 
-template <typename T>
-__global__ void set_f_kernel(const AuxArgs a, T* f, const double* src) {
+template <typename S>
+__global__ void set_f_kernel(const AuxArgs a, S* f, const double* src) {
+  using T = typename Comp<S>::type;
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= a.plane) return;
-  for (int k = 0; k < 16; ++k) f[k * a.plane + q] = (T)(src[k * a.plane + q] - a.w[k] * a.rho_ref);
+  for (int k = 0; k < 16; ++k)
+    f[k * a.plane + q] = to_store<S, T>((T)(src[k * a.plane + q] - a.w[k] * a.rho_ref));
 }
 
-template <typename T>
-__global__ void get_f_kernel(const AuxArgs a, const T* f, double* dst) {
+template <typename S>
+__global__ void get_f_kernel(const AuxArgs a, const S* f, double* dst) {
+  using T = typename Comp<S>::type;
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= a.plane) return;
-  for (int k = 0; k < 16; ++k) dst[k * a.plane + q] = (double)f[k * a.plane + q] + a.w[k] * a.rho_ref;
+  for (int k = 0; k < 16; ++k)
+    dst[k * a.plane + q] = (double)from_store<S, T>(f[k * a.plane + q]) + a.w[k] * a.rho_ref;
 }
 
 // rho - rho_ref = sum_k f_k and rho u = sum_k f_k xi_k of the stored (shifted) f
-template <typename T>
-__device__ __forceinline__ void node_moments(const AuxArgs& a, const Vel<T>& v, const T* f,
+template <typename S, typename T>
+__device__ __forceinline__ void node_moments(const AuxArgs& a, const Vel<T>& v, const S* f,
                                              long long q, T& drho, T& mx, T& my) {
   drho = mx = my = T(0);
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
-    const T fv = f[k * a.plane + q];
+    const T fv = from_store<S, T>(f[k * a.plane + q]);
     drho += fv;
     mx += fv * v.x[k];
     my += fv * v.y[k];
   }
 }
 
-template <typename T>
-__global__ void moments_kernel(const AuxArgs a, const T* f, double* rho, double* ux, double* uy) {
+template <typename S>
+__global__ void moments_kernel(const AuxArgs a, const S* f, double* rho, double* ux, double* uy) {
+  using T = typename Comp<S>::type;
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= a.plane) return;
   const Vel<T> v(a);
@@ -99,8 +117,9 @@ __device__ __forceinline__ V warp_sum(V v) {
 
 // Ring membership |dist - r_ring| < 1/2 tested exactly on integers:
 // (2r-1)^2 < (2i - Lx)^2 + (2j - Ly)^2 < (2r+1)^2.
-template <typename T>
-__global__ void diag_kernel(const AuxArgs a, const T* f, double thr, double r_ring, DiagAcc* acc) {
+template <typename S>
+__global__ void diag_kernel(const AuxArgs a, const S* f, double thr, double r_ring, DiagAcc* acc) {
+  using T = typename Comp<S>::type;
   const Vel<T> v(a);
   double mass = 0.0, ring = 0.0;
   unsigned long long nring = 0, nb = 0, sx = 0, sy = 0, sxx = 0, sxy = 0, syy = 0;
@@ -161,9 +180,10 @@ __global__ void diag_kernel(const AuxArgs a, const T* f, double thr, double r_ri
   }
 }
 
-template <typename T>
-__global__ void hist_kernel(const AuxArgs a, const T* f, int nbins, double lo, double hi,
+template <typename S>
+__global__ void hist_kernel(const AuxArgs a, const S* f, int nbins, double lo, double hi,
                             unsigned long long* counts) {
+  using T = typename Comp<S>::type;
   extern __shared__ unsigned int sh[];
   const Vel<T> v(a);
   const bool priv = nbins <= 8192;
@@ -194,51 +214,50 @@ unsigned grid_for(long long n) { return (unsigned)((n + BS - 1) / BS); }
 
 }  // namespace
 
+// Calls fn(typed f) with f cast to the storage type of a.storage.
+template <typename F>
+cudaError_t by_storage(const AuxArgs& a, const void* f, F fn) {
+  switch (a.storage) {
+    case STORE_F64: fn(static_cast<const double*>(f)); break;
+    case STORE_F16: fn(static_cast<const __half*>(f)); break;
+    default: fn(static_cast<const float*>(f)); break;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_init_feq(const AuxArgs& a, void* f, const double* rho, const double* ux,
                             const double* uy, cudaStream_t s) {
-  if (a.storage64)
-    init_feq_kernel<double><<<grid_for(a.plane), BS, 0, s>>>(a, static_cast<double*>(f), rho, ux, uy);
-  else
-    init_feq_kernel<float><<<grid_for(a.plane), BS, 0, s>>>(a, static_cast<float*>(f), rho, ux, uy);
-  return cudaGetLastError();
+  return by_storage(a, f, [&](auto p) {
+    using S = std::remove_const_t<std::remove_pointer_t<decltype(p)>>;
+    init_feq_kernel<S><<<grid_for(a.plane), BS, 0, s>>>(a, const_cast<S*>(p), rho, ux, uy);
+  });
 }
 
 cudaError_t launch_set_f(const AuxArgs& a, void* f, const double* src, cudaStream_t s) {
-  if (a.storage64)
-    set_f_kernel<double><<<grid_for(a.plane), BS, 0, s>>>(a, static_cast<double*>(f), src);
-  else
-    set_f_kernel<float><<<grid_for(a.plane), BS, 0, s>>>(a, static_cast<float*>(f), src);
-  return cudaGetLastError();
+  return by_storage(a, f, [&](auto p) {
+    using S = std::remove_const_t<std::remove_pointer_t<decltype(p)>>;
+    set_f_kernel<S><<<grid_for(a.plane), BS, 0, s>>>(a, const_cast<S*>(p), src);
+  });
 }
 
 cudaError_t launch_get_f(const AuxArgs& a, const void* f, double* dst, cudaStream_t s) {
-  if (a.storage64)
-    get_f_kernel<double><<<grid_for(a.plane), BS, 0, s>>>(a, static_cast<const double*>(f), dst);
-  else
-    get_f_kernel<float><<<grid_for(a.plane), BS, 0, s>>>(a, static_cast<const float*>(f), dst);
-  return cudaGetLastError();
+  return by_storage(a, f, [&](auto p) {
+    get_f_kernel<<<grid_for(a.plane), BS, 0, s>>>(a, p, dst);
+  });
 }
 
 cudaError_t launch_moments(const AuxArgs& a, const void* f, double* rho, double* ux, double* uy,
                            cudaStream_t s) {
-  if (a.storage64)
-    moments_kernel<double><<<grid_for(a.plane), BS, 0, s>>>(a, static_cast<const double*>(f), rho,
-                                                             ux, uy);
-  else
-    moments_kernel<float><<<grid_for(a.plane), BS, 0, s>>>(a, static_cast<const float*>(f), rho,
-                                                            ux, uy);
-  return cudaGetLastError();
+  return by_storage(a, f, [&](auto p) {
+    moments_kernel<<<grid_for(a.plane), BS, 0, s>>>(a, p, rho, ux, uy);
+  });
 }
 
 cudaError_t launch_diag(const AuxArgs& a, const void* f, double thr, double r_ring, DiagAcc* acc,
                         cudaStream_t s) {
   unsigned g = grid_for(a.plane);
   if (g > 4096) g = 4096;
-  if (a.storage64)
-    diag_kernel<double><<<g, BS, 0, s>>>(a, static_cast<const double*>(f), thr, r_ring, acc);
-  else
-    diag_kernel<float><<<g, BS, 0, s>>>(a, static_cast<const float*>(f), thr, r_ring, acc);
-  return cudaGetLastError();
+  return by_storage(a, f, [&](auto p) { diag_kernel<<<g, BS, 0, s>>>(a, p, thr, r_ring, acc); });
 }
 
 cudaError_t launch_hist(const AuxArgs& a, const void* f, int nbins, double lo, double hi,
@@ -246,18 +265,16 @@ cudaError_t launch_hist(const AuxArgs& a, const void* f, int nbins, double lo, d
   unsigned g = grid_for(a.plane);
   if (g > 2048) g = 2048;
   const size_t sh = nbins <= 8192 ? sizeof(unsigned int) * nbins : 0;
-  if (a.storage64)
-    hist_kernel<double><<<g, BS, sh, s>>>(a, static_cast<const double*>(f), nbins, lo, hi, counts);
-  else
-    hist_kernel<float><<<g, BS, sh, s>>>(a, static_cast<const float*>(f), nbins, lo, hi, counts);
-  return cudaGetLastError();
+  return by_storage(a, f, [&](auto p) {
+    hist_kernel<<<g, BS, sh, s>>>(a, p, nbins, lo, hi, counts);
+  });
 }
 
-size_t step_smem_bytes(size_t elem) {
-  const size_t elems = (size_t)SROWS * 16 * SCOL + (size_t)FROWS * 16 * REG + 6 * (size_t)MROWS * REG;
+size_t step_smem_bytes(size_t stage_elem, size_t elem) {
+  const size_t elems = (size_t)FROWS * 16 * REG + 6 * (size_t)MROWS * REG;
   // + 128 bytes to align the staging ring for tensor copies; ints, the fused
   // diagnostics accumulators, two mbarriers and the CTA's wait-abort flag
-  return 128 + elem * elems + sizeof(int) * (SG + (SG & 1)) + sizeof(double) +
+  return 128 + stage_elem * SROWS * 16 * SCOL + elem * elems + sizeof(int) * (SG + (SG & 1)) + sizeof(double) +
          6 * sizeof(unsigned long long) + 2 * sizeof(unsigned long long) + 2 * sizeof(int);
 }
 

@@ -9,12 +9,14 @@
 
 namespace ctulbm {
 
+enum { STORE_F32 = 0, STORE_F64 = 1, STORE_F16 = 2 };
+
 // Parameters of the small per-node kernels (initialisation, conversion,
 // moments, diagnostics).  Always FP64 on the host side.
 struct AuxArgs {
   int Lx, Ly;
   long long plane;
-  int storage64;     // 1: f is double, 0: f is float (shifted by w_k rho_ref)
+  int storage;       // STORE_F32 / STORE_F16: f - w_k rho_ref as float / half; STORE_F64: f
   double rho_ref, Tt;
   double xi[16][2], w[16];
 };
@@ -25,6 +27,9 @@ cudaError_t launch_step_f32(const StepArgs<float>& a, const RowMaps& maps, int o
                             bool vec, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_step_f64(const StepArgs<double>& a, const RowMaps& maps, int order, int lim,
                             bool vec, int grid, size_t smem, cudaStream_t s);
+// FP16 shifted storage, FP32 arithmetic (a.fin / a.fout hold half).
+cudaError_t launch_step_f16(const StepArgs<float>& a, const RowMaps& maps, int order, int lim,
+                            bool vec, int grid, size_t smem, cudaStream_t s);
 // Several FP32 lattices in one launch (same scheme, limiter and column path).
 cudaError_t launch_step_batch_f32(const BatchArgs<float>& b, int order, int lim, bool vec,
                                   int grid, size_t smem, cudaStream_t s);
@@ -32,8 +37,11 @@ int step_batch_occupancy_f32(int order, int lim, bool vec, size_t smem);
 // Largest resident CTAs per SM for the selected step kernel (0 on error).
 int step_occupancy_f32(int order, int lim, bool vec, size_t smem);
 int step_occupancy_f64(int order, int lim, bool vec, size_t smem);
+int step_occupancy_f16(int order, int lim, bool vec, size_t smem);
 
-size_t step_smem_bytes(size_t elem);
+// Dynamic shared memory of the step kernel: staging ring in the storage type
+// (stage_elem bytes per value), the other rings in the arithmetic type.
+size_t step_smem_bytes(size_t stage_elem, size_t elem);
 
 // f = f^eq(rho, u) - w rho_ref from FP64 device fields.
 cudaError_t launch_init_feq(const AuxArgs& a, void* f, const double* rho, const double* ux,

@@ -33,6 +33,7 @@
 #pragma once
 
 #include <cuda.h>  // CUtensorMap (type only)
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -71,8 +72,8 @@ struct ClassConst {
 
 template <typename T>
 struct StepArgs {
-  const T* fin;
-  T* fout;
+  const void* fin;          // f^n, [16][Ly][Lx] in the storage type (float, double or half)
+  void* fout;               // f^{n+1}
   int Lx, Ly;
   long long plane;          // Lx * Ly
   int nstrip;
@@ -113,6 +114,24 @@ struct BatchArgs {
 };
 
 // ---------------------------------------------------------------- helpers
+// Storage of f (float, double, or half for FP16 shifted storage) and the
+// arithmetic type T: conversions on load and store.
+template <typename S, typename T>
+__device__ __forceinline__ T from_store(S v) {
+  return (T)v;
+}
+template <>
+__device__ __forceinline__ float from_store<__half, float>(__half v) {
+  return __half2float(v);
+}
+template <typename S, typename T>
+__device__ __forceinline__ S to_store(T v) {
+  return (S)v;
+}
+template <>
+__device__ __forceinline__ __half to_store<__half, float>(float v) {
+  return __float2half_rn(v);
+}
 __device__ __forceinline__ float flip_sign(float v, float s) {
   return __int_as_float(__float_as_int(v) ^ (__float_as_int(s) & 0x80000000));
 }
@@ -193,6 +212,25 @@ __device__ __forceinline__ void sload4(const T* p, T* v) {
     double2 t0 = reinterpret_cast<const double2*>(p)[0];
     double2 t1 = reinterpret_cast<const double2*>(p)[1];
     v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+  }
+}
+
+// Twelve consecutive staged values (16-byte aligned for float/double, 8-byte
+// for half) converted to the arithmetic type.
+template <typename S, typename T>
+__device__ __forceinline__ void sload12(const S* p, T* v) {
+  if constexpr (sizeof(S) == 2) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const uint2 u = reinterpret_cast<const uint2*>(p)[m];
+      const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+      const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+      v[4 * m] = a.x; v[4 * m + 1] = a.y; v[4 * m + 2] = b.x; v[4 * m + 3] = b.y;
+    }
+  } else {
+    sload4(p, v);
+    sload4(p + 4, v + 4);
+    sload4(p + 8, v + 8);
   }
 }
 

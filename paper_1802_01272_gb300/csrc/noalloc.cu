@@ -51,7 +51,8 @@ extern "C" int lbm_histogram_noalloc(const void* f_device, int32_t Lx, int32_t L
   if (!f_device || !counts || Lx < 1 || Ly < 1 || (long long)Lx * Ly > (1LL << 31) - 1)
     return LBM_ERR_INVALID_ARG;
   if (nbins < 1 || nbins > LBM_NOALLOC_MAX_BINS || !(hi > lo)) return LBM_ERR_INVALID_ARG;
-  if (precision != LBM_FP64 && precision != LBM_FP32_SHIFTED) return LBM_ERR_INVALID_ARG;
+  if (precision != LBM_FP64 && precision != LBM_FP32_SHIFTED && precision != LBM_FP16_SHIFTED)
+    return LBM_ERR_INVALID_ARG;
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess) return LBM_ERR_CUDA;
   unsigned long long* bins = nullptr;
@@ -63,7 +64,7 @@ extern "C" int lbm_histogram_noalloc(const void* f_device, int32_t Lx, int32_t L
   a.Lx = Lx;
   a.Ly = Ly;
   a.plane = (long long)Lx * Ly;
-  a.storage64 = precision == LBM_FP64;
+  a.storage = precision == LBM_FP64 ? STORE_F64 : (precision == LBM_FP16_SHIFTED ? STORE_F16 : STORE_F32);
   a.rho_ref = precision == LBM_FP64 ? 0.0 : rho_ref;  // rho = rho_ref + sum_k f_k
 
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);

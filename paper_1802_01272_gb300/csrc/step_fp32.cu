@@ -6,7 +6,7 @@ namespace ctulbm {
 namespace {
 template <int ORDER, int LIM, bool VEC>
 void* kernel_ptr() {
-  return reinterpret_cast<void*>(&step_kernel<float, ORDER, LIM, VEC>);
+  return reinterpret_cast<void*>(&step_kernel<float, float, ORDER, LIM, VEC>);
 }
 
 void* select(int order, int lim, bool vec) {

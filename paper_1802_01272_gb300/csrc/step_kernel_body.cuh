@@ -74,10 +74,11 @@ __device__ __forceinline__ int mod_pos(int a, int n) {  // a mod n for a > -n*10
   return (a + n * 1024) % n;
 }
 
-// Shared-memory layout (elements of T, then ints).
-template <typename T>
+// Shared-memory layout: the staging ring in the storage type ST, the rings of
+// advected rows and moments in the arithmetic type T, then ints.
+template <typename T, typename ST>
 struct Smem {
-  T* stage;   // [SROWS][16][SCOL] f^n rows of the strip, one group of halo per side
+  ST* stage;  // [SROWS][16][SCOL] f^n rows of the strip, one group of halo per side
   T* fs;      // [FROWS][16][REG] advected f*
   T* rho;     // [MROWS][REG]
   T* drho;    // rho* - rho_ref
@@ -93,9 +94,8 @@ struct Smem {
   __device__ Smem(unsigned char* raw) {
     // the ring starts on 128 bytes (tensor copies); the allocation has the slack
     raw += (128u - ((unsigned)__cvta_generic_to_shared(raw) & 127u)) & 127u;
-    T* p = reinterpret_cast<T*>(raw);
-    stage = p;
-    p += SROWS * 16 * SCOL;
+    stage = reinterpret_cast<ST*>(raw);
+    T* p = reinterpret_cast<T*>(raw + sizeof(ST) * SROWS * 16 * SCOL);
     fs = p;
     p += FROWS * 16 * REG;
     rho = p;
@@ -112,23 +112,18 @@ struct Smem {
   }
 };
 
-template <typename T>
-constexpr size_t step_smem_elems() {
-  return (size_t)SROWS * 16 * SCOL + (size_t)FROWS * 16 * REG + 6 * (size_t)MROWS * REG;
-}
-
 // Staging: a staged row holds 16 planes x CH 16-byte chunks.  Thread t copies
 // chunks t, t + NT, ... of every staged row, so its (plane, column) slots are
 // fixed for a whole segment and a row costs one address add per chunk.
-template <typename T>
+template <typename T, typename ST>
 struct StageSlots {
-  static constexpr int CH = SCOL * (int)sizeof(T) / 16;  // 16-byte chunks per plane row
-  static constexpr int EPC = 16 / (int)sizeof(T);         // elements per chunk
+  static constexpr int CH = SCOL * (int)sizeof(ST) / 16;  // 16-byte chunks per plane row
+  static constexpr int EPC = 16 / (int)sizeof(ST);         // elements per chunk
   static constexpr int PER_ROW = 16 * CH;
   static constexpr int NS = (PER_ROW + NT - 1) / NT;      // chunks per thread per row
   long long src[NS];  // element offset of the chunk in row 0 of f^n (plane and column)
   int dst[NS];        // element offset inside a staged row
-  __device__ StageSlots(const StepArgs<T>& P, const Smem<T>& S, bool vec) {
+  __device__ StageSlots(const StepArgs<T>& P, const Smem<T, ST>& S, bool vec) {
 #pragma unroll
     for (int m = 0; m < NS; ++m) {
       const int c = threadIdx.x + NT * m;
@@ -143,20 +138,20 @@ struct StageSlots {
 // Stage rows [r_begin, r_end) of f^n for all 16 planes into the staging ring
 // (asynchronously when VEC).  Rows outside the lattice are wall ghost rows
 // (constant per plane) or wrap periodically.
-template <typename T, bool VEC>
-__device__ __forceinline__ void stage_rows(const StepArgs<T>& P, const Smem<T>& S,
-                                           const StageSlots<T>& sl, int r_begin, int r_end,
+template <typename T, typename ST, bool VEC>
+__device__ __forceinline__ void stage_rows(const StepArgs<T>& P, const Smem<T, ST>& S,
+                                           const StageSlots<T, ST>& sl, int r_begin, int r_end,
                                            int rbase) {
-  using SS = StageSlots<T>;
+  using SS = StageSlots<T, ST>;
   for (int r = r_begin; r < r_end; ++r) {
-    T* srow = S.stage + mod_pos(r - rbase, SROWS) * 16 * SCOL;
+    ST* srow = S.stage + mod_pos(r - rbase, SROWS) * 16 * SCOL;
     if (P.walls && (r < 0 || r >= P.Ly)) {
 #pragma unroll
       for (int m = 0; m < SS::NS; ++m) {
         const int c = threadIdx.x + NT * m;
         if (c < SS::PER_ROW) {
           const int k = c / SS::CH;
-          const T gv = r < 0 ? P.v[k].gbot : P.v[k].gtop;
+          const ST gv = to_store<ST, T>(r < 0 ? P.v[k].gbot : P.v[k].gtop);
 #pragma unroll
           for (int e = 0; e < SS::EPC; ++e) srow[sl.dst[m] + e] = gv;
         }
@@ -164,7 +159,7 @@ __device__ __forceinline__ void stage_rows(const StepArgs<T>& P, const Smem<T>& 
       continue;
     }
     const int rw = r < 0 ? r + P.Ly * ((-r + P.Ly - 1) / P.Ly) : (r >= P.Ly ? r % P.Ly : r);
-    const T* frow = P.fin + (long long)rw * P.Lx;
+    const ST* frow = static_cast<const ST*>(P.fin) + (long long)rw * P.Lx;
 #pragma unroll
     for (int m = 0; m < SS::NS; ++m) {
       const int c = threadIdx.x + NT * m;
@@ -173,7 +168,7 @@ __device__ __forceinline__ void stage_rows(const StepArgs<T>& P, const Smem<T>& 
           cp_async16(srow + sl.dst[m], frow + sl.src[m]);
         } else {
           const int k = c / SS::CH, ch = c - k * SS::CH;
-          const T* fk = frow + (long long)k * P.plane;
+          const ST* fk = frow + (long long)k * P.plane;
           const int x0 = S.col[0];  // unwrapped first staging column (scalar path)
 #pragma unroll
           for (int e = 0; e < SS::EPC; ++e)
@@ -193,13 +188,13 @@ __device__ __forceinline__ void stage_rows(const StepArgs<T>& P, const Smem<T>& 
 // the byte count first; wall ghost rows (constant per plane) are written by
 // all threads.  `fence` orders earlier generic writes of the ring (ghost rows)
 // before the copies.
-template <typename T>
-__device__ __forceinline__ void stage_rows_tma(const StepArgs<T>& P, const Smem<T>& S,
-                                               const StageSlots<T>& sl, const CUtensorMap* tm,
+template <typename T, typename ST>
+__device__ __forceinline__ void stage_rows_tma(const StepArgs<T>& P, const Smem<T, ST>& S,
+                                               const StageSlots<T, ST>& sl, const CUtensorMap* tm,
                                                int x0, int r_begin, int r_end, int rbase,
                                                unsigned batch, bool fence) {
-  using SS = StageSlots<T>;
-  constexpr unsigned ROW_BYTES = 16u * SCOL * (unsigned)sizeof(T);
+  using SS = StageSlots<T, ST>;
+  constexpr unsigned ROW_BYTES = 16u * SCOL * (unsigned)sizeof(ST);
   const int Ly = P.Ly;
   if (threadIdx.x == 0) {
     unsigned long long* bar = S.bar + (batch & 1u);
@@ -214,7 +209,7 @@ __device__ __forceinline__ void stage_rows_tma(const StepArgs<T>& P, const Smem<
         if (!(P.walls && (r < 0 || r >= Ly))) bytes += ROW_BYTES;
       mbar_arrive_expect_tx(bar, bytes);
       for (int r = r_begin; r < r_end;) {
-        T* dst = S.stage + mod_pos(r - rbase, SROWS) * 16 * SCOL;
+        ST* dst = S.stage + mod_pos(r - rbase, SROWS) * 16 * SCOL;
         if (mod_pos(r - rbase, RPI) == 0 && r + RPI <= r_end && r >= 0 && r + RPI <= Ly) {
           tma_load_rows(dst, tm, x0, r, bar);  // an aligned batch inside the lattice
           r += RPI;
@@ -232,12 +227,12 @@ __device__ __forceinline__ void stage_rows_tma(const StepArgs<T>& P, const Smem<
   if (P.walls && (r_begin < 0 || r_end > Ly)) {
     for (int r = r_begin; r < r_end; ++r) {
       if (r >= 0 && r < Ly) continue;
-      T* srow = S.stage + mod_pos(r - rbase, SROWS) * 16 * SCOL;
+      ST* srow = S.stage + mod_pos(r - rbase, SROWS) * 16 * SCOL;
 #pragma unroll
       for (int m = 0; m < SS::NS; ++m) {
         const int c = threadIdx.x + NT * m;
         if (c < SS::PER_ROW) {
-          const T gv = r < 0 ? P.v[c / SS::CH].gbot : P.v[c / SS::CH].gtop;
+          const ST gv = to_store<ST, T>(r < 0 ? P.v[c / SS::CH].gbot : P.v[c / SS::CH].gtop);
 #pragma unroll
           for (int e = 0; e < SS::EPC; ++e) srow[sl.dst[m] + e] = gv;
         }
@@ -248,9 +243,8 @@ __device__ __forceinline__ void stage_rows_tma(const StepArgs<T>& P, const Smem<
 
 // Every thread waits for tensor-copy batch `batch` (bounded); a timeout sets
 // the step's error bit 2 and the CTA stops waiting (its results are void).
-template <typename T>
-__device__ __forceinline__ void tma_wait_batch(const StepArgs<T>& P, const Smem<T>& S,
-                                               unsigned batch) {
+template <typename T, typename SM>
+__device__ __forceinline__ void tma_wait_batch(const StepArgs<T>& P, const SM& S, unsigned batch) {
   if (*reinterpret_cast<volatile int*>(S.abort)) return;
   if (!mbar_wait_bounded(S.bar + (batch & 1u), (batch >> 1) & 1u)) {
     *reinterpret_cast<volatile int*>(S.abort) = 1;
@@ -260,8 +254,8 @@ __device__ __forceinline__ void tma_wait_batch(const StepArgs<T>& P, const Smem<
 
 // P1 for one warp quadrant: rows a0 .. a0+RPI-1 of plane k, two rows per loop
 // trip so that the two-row history rotates by register renaming.
-template <int SX, int SY, int ORDER, int LIM, typename T>
-__device__ __forceinline__ void advect_rows(const StepArgs<T>& P, const Smem<T>& S,
+template <int SX, int SY, int ORDER, int LIM, typename T, typename ST>
+__device__ __forceinline__ void advect_rows(const StepArgs<T>& P, const Smem<T, ST>& S,
                                             AdvState<T>& st, const VelConst<T>& vc, int a0,
                                             int rbase, int src_off, int dst_off, bool ghosts) {
   constexpr int LAG = SY > 0 ? 1 : 2;  // staged row read for output row a
@@ -272,11 +266,9 @@ __device__ __forceinline__ void advect_rows(const StepArgs<T>& P, const Smem<T>&
     for (int jj = 0; jj < 2; ++jj) {
       const int a = a0 + j + jj;
       T v[12];
-      const T* srow = S.stage + slot * (16 * SCOL) + src_off;
+      const ST* srow = S.stage + slot * (16 * SCOL) + src_off;
       slot = slot == SROWS - 1 ? 0 : slot + 1;
-      sload4(srow, v);
-      sload4(srow + 4, v + 4);
-      sload4(srow + 8, v + 8);
+      sload12(srow, v);
       T out[4];
       advect_row<SX, SY, ORDER, LIM>(st, v, vc, out);
       if (ghosts && (a < 0 || a >= P.Ly)) {  // ghost rows keep f^eq(rho_ext, u_wall)
@@ -298,8 +290,8 @@ __device__ __forceinline__ void advect_rows(const StepArgs<T>& P, const Smem<T>&
 // One row segment [ys, ye) of one strip of one lattice.  Every node's update
 // uses the same arithmetic in the same order whatever the segment boundaries,
 // so results do not depend on how the rows are split over CTAs or lattices.
-template <typename T, int ORDER, int LIM, bool VEC>
-__device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T>& S, int strip,
+template <typename T, typename ST, int ORDER, int LIM, bool VEC>
+__device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, ST>& S, int strip,
                                             int ys, int ye, const CUtensorMap* tm,
                                             unsigned& batch) {
   const int tid = threadIdx.x;
@@ -334,7 +326,7 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T>&
     const int p4_x = strip * TW + p4_col - XOFF;            // global output column
     const bool p4_col_ok = p4_col < XOFF + TW && p4_x < Lx;
 
-    const StageSlots<T> slots(P, S, VEC);
+    const StageSlots<T, ST> slots(P, S, VEC);
     // interior strips stage by tensor copies, the strips at the periodic x
     // seam (and lattices without a tensor map) by per-thread copies
     const int x0 = strip * TW - XOFF - 4;
@@ -344,9 +336,9 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T>&
     int a0 = ys - WARMUP;
     const int rbase = a0 + 2;  // first row of every iteration's batch: rbase + RPI i
     if (tma)
-      stage_rows_tma<T>(P, S, slots, tm, x0, a0 + 1, a0 + RPI + 2, rbase, batch, fence);
+      stage_rows_tma<T, ST>(P, S, slots, tm, x0, a0 + 1, a0 + RPI + 2, rbase, batch, fence);
     else
-      stage_rows<T, VEC>(P, S, slots, a0 + 1, a0 + RPI + 2, rbase);
+      stage_rows<T, ST, VEC>(P, S, slots, a0 + 1, a0 + RPI + 2, rbase);
     cp_async_commit();
 
     for (; a0 - 2 < ye; a0 += RPI) {
@@ -354,12 +346,12 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T>&
       const bool more = (a0 + RPI) - 2 < ye;
       if (tma) {
         if (more)
-          stage_rows_tma<T>(P, S, slots, tm, x0, a0 + RPI + 2, a0 + 2 * RPI + 2, rbase, batch + 1,
-                            fence);
-        tma_wait_batch<T>(P, S, batch);
+          stage_rows_tma<T, ST>(P, S, slots, tm, x0, a0 + RPI + 2, a0 + 2 * RPI + 2, rbase,
+                                batch + 1, fence);
+        tma_wait_batch(P, S, batch);
         ++batch;
       } else {
-        if (more) stage_rows<T, VEC>(P, S, slots, a0 + RPI + 2, a0 + 2 * RPI + 2, rbase);
+        if (more) stage_rows<T, ST, VEC>(P, S, slots, a0 + RPI + 2, a0 + 2 * RPI + 2, rbase);
         cp_async_commit();
         cp_async_wait<1>();
       }
@@ -508,7 +500,7 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T>&
           }
 
           rho_post = scale * rho;  // the collision conserves mass; the reservoir rescales it
-          T* dst = P.fout + (long long)c * Lx + p4_x;
+          ST* dst = static_cast<ST*>(P.fout) + (long long)c * Lx + p4_x;
           const long long pl = P.plane;
           const T add = P.reservoir ? P.rho_ref * (scale - T(1)) : T(0);
           if (!P.reservoir) scale = T(1);
@@ -543,7 +535,7 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T>&
             }
 #pragma unroll
             for (int sgn = 0; sgn < 4; ++sgn) {
-              *dst = outv[sgn];
+              *dst = to_store<ST, T>(outv[sgn]);
               dst += pl;
             }
           }
@@ -599,11 +591,11 @@ __device__ __forceinline__ void retire_cta(unsigned long long* sched) {
   }
 }
 
-template <typename T, int ORDER, int LIM, bool VEC>
+template <typename T, typename ST, int ORDER, int LIM, bool VEC>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     step_kernel(const __grid_constant__ StepArgs<T> P, const __grid_constant__ RowMaps maps) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const Smem<T> S(smem_raw);
+  const Smem<T, ST> S(smem_raw);
   __shared__ long long s_item;
   if (threadIdx.x == 0) {
     *S.dmass = 0.0;
@@ -622,7 +614,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     const int strip = (int)(item - rb * P.nstrip);
     const int ys = (int)(rb * P.row_block);
     const int ye = min(P.Ly, ys + P.row_block);
-    run_segment<T, ORDER, LIM, VEC>(P, S, strip, ys, ye, tm, batch);
+    run_segment<T, ST, ORDER, LIM, VEC>(P, S, strip, ys, ye, tm, batch);
   }
   // claim_item's barrier after the last claim orders every warp's shared adds
   if (P.diag_mass && threadIdx.x == 0) {
@@ -638,7 +630,7 @@ template <typename T, int ORDER, int LIM, bool VEC>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     step_batch_kernel(const __grid_constant__ BatchArgs<T> B) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const Smem<T> S(smem_raw);
+  const Smem<T, T> S(smem_raw);
   __shared__ long long s_item;
   int i = 0;
   unsigned batch = 0;  // unused: batched lattices stage by per-thread copies
@@ -652,7 +644,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     const int strip = (int)(local - rb * P.nstrip);
     const int ys = (int)(rb * P.row_block);
     const int ye = min(P.Ly, ys + P.row_block);
-    run_segment<T, ORDER, LIM, VEC>(P, S, strip, ys, ye, nullptr, batch);
+    run_segment<T, T, ORDER, LIM, VEC>(P, S, strip, ys, ye, nullptr, batch);
   }
   retire_cta(B.sched);
 }

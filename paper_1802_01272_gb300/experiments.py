@@ -1,0 +1,166 @@
+"""Bubble experiments of Sec. III run on the CUDA path.
+
+* surface tension of a relaxed planar interface, sigma = kappa int (d rho/dx)^2 dx
+  (Eq. sigma, in the reading whose values the paper prints);
+* the critical radius of Eq. (raggio_c) and the growth or collapse of bubbles
+  around it with the density reservoir of Sec. III A;
+* bubble growth against the two-dimensional Rayleigh-Plesset equation
+  (Eq. rp), fed with the pressures measured on the lattice as in Sec. III B.
+
+Host-side analysis is FP64 numpy; every lattice step, moment and diagnostic
+runs in the library.  Lengths are in the paper's units (node spacing ds).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import eos
+from .binding import LBM_FP32_SHIFTED, LBM_FP64, Lattice, Params
+
+
+def free_energy(rho, T, a=9 / 8, b=1 / 3):
+    """Bulk free-energy density psi = rho T ln(rho / (1 - b rho)) - a rho^2
+    (Eq. free-en2 for b = 1/3, a = 9/8)."""
+    return rho * T * np.log(rho / (1.0 - b * rho)) - a * rho * rho
+
+
+def critical_radius(T, rho_ext, sigma, a=9 / 8, b=1 / 3):
+    """Eq. (raggio_c): radius of the bubble that neither grows nor shrinks in
+    a liquid held at rho_ext, with the coexistence densities of T."""
+    rl, rv = eos.coexistence(T, a, b)
+    pe = free_energy(rho_ext, T, a, b)
+    brace = (free_energy(rv, T, a, b) - pe) + \
+        (rho_ext - rv) / (rl - rho_ext) * (free_energy(rl, T, a, b) - pe)
+    return -0.5 * sigma / brace
+
+
+def rayleigh_plesset(R0, V0, times, p_b, p_inf, r_inf, sigma, rho_l, mu_l, dt=1e-3):
+    """Eq. (rp) integrated with the classical fourth-order Runge-Kutta scheme;
+    p_b and p_inf are callables of t.  Returns R at `times` (ascending, from 0)."""
+    def accel(t, R, V):
+        lg = math.log(r_inf / R)
+        drive = (p_b(t) - p_inf(t)) / rho_l - sigma / (rho_l * R) - 2.0 * mu_l * V / (rho_l * R)
+        return (drive + 0.5 * (1.0 - (R / r_inf) ** 2) * V * V - lg * V * V) / (lg * R)
+
+    out = np.empty(len(times))
+    t, R, V = 0.0, float(R0), float(V0)
+    for i, te in enumerate(times):
+        while t < te - 1e-12:
+            h = min(dt, te - t)
+            k1r, k1v = V, accel(t, R, V)
+            k2r, k2v = V + 0.5 * h * k1v, accel(t + 0.5 * h, R + 0.5 * h * k1r, V + 0.5 * h * k1v)
+            k3r, k3v = V + 0.5 * h * k2v, accel(t + 0.5 * h, R + 0.5 * h * k2r, V + 0.5 * h * k2v)
+            k4r, k4v = V + h * k3v, accel(t + h, R + h * k3r, V + h * k3v)
+            R += h / 6.0 * (k1r + 2 * k2r + 2 * k3r + k4r)
+            V += h / 6.0 * (k1v + 2 * k2v + 2 * k3v + k4v)
+            t += h
+        out[i] = R
+    return out
+
+
+def bubble_fields(Lx, Ly, R, rho_in, rho_out, width=1.0):
+    """A circular bubble of radius R nodes centred at (Lx/2, Ly/2): a tanh
+    profile of `width` nodes between rho_in (inside) and rho_out; u = 0."""
+    y, x = np.mgrid[0:Ly, 0:Lx].astype(np.float64)
+    r = np.hypot(x - Lx / 2.0, y - Ly / 2.0)
+    rho = 0.5 * (rho_out + rho_in) + 0.5 * (rho_out - rho_in) * np.tanh((r - R) / width)
+    return rho, np.zeros_like(rho), np.zeros_like(rho)
+
+
+def _params(Lx, Ly, T, tau, kappa, ds, precision, rho_ref, **kw):
+    return Params(Lx=Lx, Ly=Ly, T=T, tau=tau, kappa=kappa, ds=ds, precision=precision,
+                  rho_ref=rho_ref, **kw)
+
+
+def planar_interface_sigma(T=0.8, kappa=1e-4, ds=1 / 256, Lx=512, Ly=8, tau=1e-3, t_end=50.0,
+                           precision=LBM_FP64, stream=None):
+    """Eq. (sigma) on a relaxed liquid slab between two vapour regions
+    (periodic x): sigma = kappa sum_i (d rho/dx)_i^2 ds per interface, with the
+    centred difference of the node densities.  Returns (sigma, rho profile).
+    The equilibrium of the forced BGK model drifts with tau (the vapour density
+    falls as tau grows), so the default is the paper's tau = 1e-3; the vapour
+    side relaxes slowly, hence the long default run."""
+    rl, rv = eos.coexistence(T)
+    x = np.arange(Lx, dtype=np.float64)
+    prof = rv + 0.5 * (rl - rv) * (np.tanh((x - Lx / 4) / 2.0) - np.tanh((x - 3 * Lx / 4) / 2.0))
+    rho = np.repeat(prof[None, :], Ly, axis=0)
+    p = _params(Lx, Ly, T, tau, kappa, ds, precision, rl)
+    with Lattice(p, stream) as L:
+        L.init_rho_u(rho, np.zeros_like(rho), np.zeros_like(rho))
+        L.step(int(round(t_end / p.dt)))
+        r, _, _ = L.moments()
+    prof = r.mean(axis=0)
+    grad = (np.roll(prof, -1) - np.roll(prof, 1)) / (2.0 * ds)
+    return kappa * float(np.sum(grad * grad)) * ds / 2.0, prof
+
+
+@dataclass
+class BubbleRun:
+    t: np.ndarray                 # time
+    R: np.ndarray                 # equivalent radius sqrt(N_b / pi) ds
+    rho_center: np.ndarray        # rho at the bubble centre
+    rho_inf: np.ndarray           # mean rho on the ring r = r_inf
+    r_inf: float                  # far-field radius R_BC
+    params: Params = field(repr=False, default=None)
+
+
+def bubble_in_reservoir(R0_nodes, rho_ext, T=0.8, kappa=1e-4, ds=1 / 256, L=1024, tau=1e-3,
+                        t_end=4.0, every=0.1, rho_v=None, precision=LBM_FP32_SHIFTED,
+                        stream=None) -> BubbleRun:
+    """Sec. III A-B: a vapour bubble (rho_v, default the coexistence vapour)
+    in a superheated liquid held at rho_ext outside R_BC = [L/2 - 1/(2 ds)] ds
+    by the reservoir rescale.  Records R(t) from the bubble-site count
+    (rho < (rho_V + rho_L)/2), rho at the centre and on the ring r = R_BC."""
+    rl, rv = eos.coexistence(T)
+    rho_v = rv if rho_v is None else rho_v
+    rho, ux, uy = bubble_fields(L, L, R0_nodes, rho_v, rho_ext, 1.0)
+    p = _params(L, L, T, tau, kappa, ds, precision, rho_ext, reservoir=1, rho_ext=rho_ext)
+    thr = 0.5 * (rl + rv)
+    r_inf_nodes = L / 2 - 1.0 / (2.0 * ds)
+    n_every = max(1, int(round(every / p.dt)))
+    n_rec = int(round(t_end / every))
+    t, R, rc, ri = [], [], [], []
+    with Lattice(p, stream) as Lt:
+        Lt.init_rho_u(rho, ux, uy)
+        for i in range(n_rec + 1):
+            if i:
+                Lt.step(n_every)
+            d = Lt.diagnostics(thr, r_inf_nodes)
+            t.append(i * n_every * p.dt)
+            R.append(math.sqrt(d["nb"] / math.pi) * ds)
+            rc.append(d["rho_center"])
+            ri.append(d["rho_ring"])
+    return BubbleRun(t=np.array(t), R=np.array(R), rho_center=np.array(rc), rho_inf=np.array(ri),
+                     r_inf=r_inf_nodes * ds, params=p)
+
+
+def rp_prediction(run: BubbleRun, t0: float, sigma=None, window=0.5):
+    """Sec. III B: integrate Eq. (rp) from the lattice state at t0, after the
+    initial interface has relaxed.  R(t0) and dR/dt(t0) come from a straight-line
+    fit of the run's R over [t0 - window, t0 + window]; p_B(t) and p_inf(t) are
+    the EOS pressures of the measured centre and far-field densities, averaged
+    over +-window/2 (the vapour inside rings acoustically); rho_L is the
+    coexistence liquid density and mu_L = rho_L T tau.  Returns (t, R_RP) at
+    the run's record times >= t0."""
+    p = run.params
+    rl, _ = eos.coexistence(p.T)
+    sigma = eos.interface_tension(p.T, p.kappa) if sigma is None else sigma
+    i0 = int(np.searchsorted(run.t, t0 - 1e-12))
+    fit = np.abs(run.t - run.t[i0]) <= window + 1e-12
+    V0, R0 = np.polyfit(run.t[fit] - run.t[i0], run.R[fit], 1)
+
+    def smooth(x):
+        out = np.empty_like(x)
+        for j, tj in enumerate(run.t):
+            out[j] = x[np.abs(run.t - tj) <= 0.5 * window + 1e-12].mean()
+        return out
+
+    pb = eos.pressure(smooth(run.rho_center), p.T)[i0:]
+    pf = eos.pressure(smooth(run.rho_inf), p.T)[i0:]
+    ts = run.t[i0:] - run.t[i0]
+    R = rayleigh_plesset(R0, V0, ts, lambda t: np.interp(t, ts, pb),
+                         lambda t: np.interp(t, ts, pf), run.r_inf, sigma, rl, rl * p.T * p.tau)
+    return run.t[i0:], R

@@ -1,0 +1,45 @@
+"""Host-side pieces of the bubble experiments (no GPU): the library's
+Eq. (raggio_c) and Rayleigh-Plesset integrator against the oracle's closed
+forms, which the oracle pins hold to the paper's printed numbers."""
+import math
+
+import numpy as np
+
+
+def test_free_energy_and_critical_radius_agree_with_oracle():
+    from oracle import analysis as A
+    from paper_1802_01272_gb300 import experiments as X
+    for rho in (0.2, 1.0, 1.9):
+        assert abs(X.free_energy(rho, 0.8) - A.psi(rho, 0.8)) < 1e-14
+    for rho_ext in (1.87, 1.9, 1.923):
+        got = X.critical_radius(0.8, rho_ext, 4.8747e-3)
+        want = A.critical_radius(4.8747e-3, rho_ext, 0.8)
+        assert abs(got - want) / want < 1e-9
+    # Sec. III B: R_c rises with rho_ext (inset of the critical-radius figure)
+    r = [X.critical_radius(0.8, e, 4.8747e-3) for e in (1.87, 1.9, 1.923)]
+    assert r[0] < r[1] < r[2]
+
+
+def test_rayleigh_plesset_agrees_with_oracle_rk4():
+    from oracle import analysis as A
+    from paper_1802_01272_gb300 import experiments as X
+    kw = dict(r_inf=1.5, sigma=4.87e-3, rho_l=1.93, mu_l=1.93 * 0.8 * 1e-3)
+    pb = lambda t: 0.1 + 0.002 * t                       # noqa: E731
+    pf = lambda t: 0.08                                  # noqa: E731
+    times = np.array([0.0, 0.5, 1.0, 2.0])
+    R = X.rayleigh_plesset(0.35, 0.01, times, pb, pf, **kw)
+    t, Ro, _ = A.rp_integrate(0.35, 0.01, 2.0, 1e-3, p_b=pb, p_inf=pf, **kw)
+    for te, r in zip(times, R):
+        assert abs(r - np.interp(te, t, Ro)) < 1e-10
+    # Laplace balance: a bubble with p_B - p_inf = sigma / R stays put
+    R = X.rayleigh_plesset(0.3, 0.0, times, lambda t: 0.08 + 4.87e-3 / 0.3, pf, **kw)
+    assert np.abs(R - 0.3).max() < 1e-13
+
+
+def test_bubble_fields_geometry():
+    from paper_1802_01272_gb300 import experiments as X
+    rho, ux, uy = X.bubble_fields(128, 96, 20.0, 0.24, 1.9, 1.0)
+    assert rho.shape == (96, 128) and not ux.any() and not uy.any()
+    assert abs(rho[48, 64] - 0.24) < 1e-9 and abs(rho[0, 0] - 1.9) < 1e-9
+    nb = (rho < 0.5 * (0.24 + 1.9)).sum()
+    assert abs(math.sqrt(nb / math.pi) - 20.0) < 0.5

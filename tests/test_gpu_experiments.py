@@ -1,0 +1,80 @@
+"""Sec. III bubble experiments on the CUDA path: surface tension of a planar
+interface, the critical radius of Eq. (raggio_c) and bubble growth against the
+Rayleigh-Plesset equation (Eq. rp)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from tests.conftest import has_gpu
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not has_gpu(), reason="needs a CUDA GPU")]
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def test_planar_interface_surface_tension():
+    """Sec. III A: sigma of the relaxed planar interface at T = 0.8, kappa = 1e-4,
+    ds = 1/256, tau = 1e-3 (the paper: 4.8747e-3; ours is 1 % lower, within the
+    spread of numerical derivatives over an 11-node interface).  The liquid
+    plateau sits on the Maxwell density; the vapour plateau 3.4 % below it (the
+    paper reports LB densities that approach the Maxwell values as tau -> 0,
+    Sec. II E)."""
+    from paper_1802_01272_gb300 import eos
+    from paper_1802_01272_gb300 import experiments as X
+    sigma, prof = X.planar_interface_sigma()
+    want = GOLD["surface_tension_T0.8_kappa1e-4"]["ds_1_256"]
+    rl, rv = eos.coexistence(0.8)
+    print(f"\nsigma planar = {sigma:.6e} paper {want:.6e} rel {(sigma - want) / want:+.2e}; "
+          f"rho_L {prof.max():.6f} ({rl:.6f}) rho_V {prof.min():.6f} ({rv:.6f})")
+    assert abs(sigma - want) / want < 2e-2
+    assert abs(prof.max() - rl) / rl < 1e-3 and abs(prof.min() - rv) / rv < 5e-2
+
+
+def test_coexistence_approaches_maxwell_as_tau_decreases():
+    """Sec. II E (dependence of rho_L, rho_V on tau at T = 0.8): the planar
+    interface's vapour density moves toward the Maxwell value as tau falls."""
+    from paper_1802_01272_gb300 import eos
+    from paper_1802_01272_gb300 import experiments as X
+    _, rv = eos.coexistence(0.8)
+    dev = []
+    for tau in (1e-2, 1e-3):
+        _, prof = X.planar_interface_sigma(tau=tau, t_end=30.0)
+        dev.append(abs(prof.min() - rv) / rv)
+        print(f"\ntau={tau}: rho_V {prof.min():.6f} (Maxwell {rv:.6f}) rel {dev[-1]:.3e}")
+    assert dev[1] < dev[0]
+
+
+def test_critical_radius_brackets_growth_and_collapse():
+    """Sec. III A: with the liquid held at rho_ext = 1.923 (T = 0.8), a bubble
+    below Eq. (raggio_c)'s radius (75.7 ds) collapses and one above it grows."""
+    from paper_1802_01272_gb300 import eos
+    from paper_1802_01272_gb300 import experiments as X
+    rc = X.critical_radius(0.8, 1.923, eos.interface_tension(0.8, 1e-4)) * 256
+    print(f"\nR_c pred = {rc:.2f} nodes")
+    small = X.bubble_in_reservoir(rc - 15, 1.923, t_end=4.0, every=0.25)
+    large = X.bubble_in_reservoir(rc + 25, 1.923, t_end=4.0, every=0.25)
+    print("small R(t) nodes", np.round(small.R * 256, 2))
+    print("large R(t) nodes", np.round(large.R * 256, 2))
+    i = int(np.searchsorted(small.t, 1.0))
+    assert small.R[-1] * 256 < small.R[i] * 256 - 2.0
+    assert large.R[-1] * 256 > large.R[i] * 256 + 1.0
+
+
+def test_rayleigh_plesset_growth():
+    """Sec. III B: a supercritical bubble (rho_ext = 1.923) grows as Eq. (rp)
+    predicts from the pressures measured at its centre and at r_inf = R_BC,
+    starting from the lattice state after the interface has relaxed (t = 2);
+    2048^2 nodes, so that r_inf / R stays large (the paper notes RP holds only
+    while that ratio is large)."""
+    from paper_1802_01272_gb300 import experiments as X
+    run = X.bubble_in_reservoir(110, 1.923, L=2048, t_end=8.0, every=0.1)
+    t, R = X.rp_prediction(run, 2.0)
+    lb = run.R[np.searchsorted(run.t, t[0] - 1e-12):]
+    print("\nt", np.round(t[::10], 2))
+    print("R_LB nodes", np.round(lb[::10] * 256, 2))
+    print("R_RP nodes", np.round(R[::10] * 256, 2))
+    growth = lb[-1] - lb[0]
+    assert growth * 256 > 3.0
+    assert abs(R[-1] - lb[-1]) < 0.25 * growth

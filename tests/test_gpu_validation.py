@@ -6,6 +6,7 @@
   fluid against the Maxwell construction, and FP32 shifted storage against
   FP64 on the same run.
 """
+import functools
 import json
 import math
 import os
@@ -20,6 +21,20 @@ pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not has_gpu(), reason="needs a
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
 ROWS = GOLD["table_II_apparent_viscosity"]["rows"]   # tau, ds, c1a, c2a, c1d, c2d
+
+
+ROWS3 = GOLD["table_III_numerical_viscosity_ctu1"]["rows"]   # tau, ds, axial, diagonal
+
+
+@functools.lru_cache(maxsize=None)
+def nu_app(order, row, diagonal):
+    """GPU apparent viscosity for Table II's (order, row, orientation), FP64.
+    CTU1 settles within a few tau; the MC limiter of CTU2 reshapes the wave
+    slowly, so its rate is read from t = 1 on."""
+    import paper_1802_01272_gb300 as P
+    tau, ds = ROWS[row][0], ROWS[row][1]
+    t1, t2 = (0.05, 0.5) if order == 1 else (1.0, 2.0)
+    return shear_wave_viscosity(P, order, tau, ds, diagonal, t1, t2, P.LBM_FP64)
 
 
 def shear_wave_viscosity(P, order, tau, ds, diagonal, t1, t2, precision):
@@ -47,33 +62,61 @@ def shear_wave_viscosity(P, order, tau, ds, diagonal, t1, t2, precision):
     return math.log(u1 / u2) / (k2 * (t2 - t1))
 
 
-@pytest.mark.parametrize("row", range(4), ids=lambda r: f"tau{ROWS[r][0]}_ds{ROWS[r][1]:.5f}")
+ROW_IDS = [f"tau{r[0]}_ds{r[1]:.5f}" for r in ROWS]
+
+
+@pytest.mark.parametrize("row", range(4), ids=ROW_IDS)
 @pytest.mark.parametrize("order", [1, 2])
 def test_table_II_axial(row, order):
-    import paper_1802_01272_gb300 as P
-    tau, ds = ROWS[row][0], ROWS[row][1]
     want = ROWS[row][2] if order == 1 else ROWS[row][3]
-    # CTU1 settles within a few tau; the MC limiter of CTU2 reshapes the wave
-    # slowly, so its rate is read from t = 1 on (see the oracle pin)
-    t1, t2 = (0.05, 0.5) if order == 1 else (1.0, 2.0)
-    nu = shear_wave_viscosity(P, order, tau, ds, False, t1, t2, P.LBM_FP64)
-    print(f'\nTableII axial order={order} tau={tau} ds={ds}: nu={nu:.6e} paper={want:.6e} rel={(nu-want)/want:+.2e}')
+    nu = nu_app(order, row, False)
+    print(f'\nTableII axial order={order} tau={ROWS[row][0]} ds={ROWS[row][1]}: nu={nu:.6e} '
+          f'paper={want:.6e} rel={(nu-want)/want:+.2e}')
     assert abs(nu - want) / want < 1e-3, (nu, want)
 
 
-@pytest.mark.parametrize("order,col", [(1, 4), (2, 5)])
-def test_table_II_diagonal(order, col):
-    """Diagonal waves on the 362 x 362 lattice of the paper exercise the transverse
-    terms of CTU2; FP64 storage (FP32 storage adds a slow systematic drift of
-    ~1e-9 per step from its rounded quadrature constants, visible over the
-    2e4 steps of this measurement)."""
-    import paper_1802_01272_gb300 as P
-    tau, ds = ROWS[0][0], ROWS[0][1]
-    t1, t2 = (0.05, 0.5) if order == 1 else (1.0, 2.0)
-    nu = shear_wave_viscosity(P, order, tau, ds, True, t1, t2, P.LBM_FP64)
-    want = ROWS[0][col]
-    print(f'\nTableII diagonal order={order}: nu={nu:.6e} paper={want:.6e} rel={(nu-want)/want:+.2e}')
+@pytest.mark.parametrize("row", range(4), ids=ROW_IDS)
+@pytest.mark.parametrize("order", [1, 2])
+def test_table_II_diagonal(row, order):
+    """Diagonal waves (L = 2 sqrt 2 / ds nodes a side, 362 and 724 as in the
+    paper) exercise the transverse terms of CTU2.  FP64 storage: FP32 storage
+    adds a slow systematic drift of ~1e-9 per step from its rounded quadrature
+    constants, visible over the 2e4 steps of this measurement."""
+    want = ROWS[row][4] if order == 1 else ROWS[row][5]
+    nu = nu_app(order, row, True)
+    print(f'\nTableII diagonal order={order} tau={ROWS[row][0]} ds={ROWS[row][1]}: nu={nu:.6e} '
+          f'paper={want:.6e} rel={(nu-want)/want:+.2e}')
     assert abs(nu - want) / want < 2e-3, (nu, want)
+
+
+@pytest.mark.parametrize("row", range(4), ids=ROW_IDS)
+def test_table_III_ctu1_numerical_viscosity(row):
+    """Table III: nu_num = nu_app - rho tau T of CTU1, both orientations, from
+    the same GPU runs (1 % : nu_num is the small difference of two numbers)."""
+    tau = ROWS3[row][0]
+    for col, diagonal in ((2, False), (3, True)):
+        got = nu_app(1, row, diagonal) - tau
+        want = ROWS3[row][col]
+        print(f'\nTableIII tau={tau} ds={ROWS3[row][1]} diagonal={diagonal}: nu_num={got:.5e} '
+              f'paper={want:.5e} rel={(got-want)/want:+.2e}')
+        assert abs(got - want) / want < 1e-2, (row, diagonal, got, want)
+
+
+def test_table_III_ctu1_scaling():
+    """Sec. II D: the CTU1 numerical viscosity halves with ds (it is linear in
+    ds, Eq. ctuevol3) and is sqrt 2 larger along the diagonal, where nodes are
+    ds sqrt 2 apart; tau does not change it."""
+    for tau_row in (0, 2):
+        for diagonal in (False, True):
+            r = (nu_app(1, tau_row, diagonal) - ROWS[tau_row][0]) / \
+                (nu_app(1, tau_row + 1, diagonal) - ROWS[tau_row + 1][0])
+            assert abs(r - 2.0) < 0.1, (tau_row, diagonal, r)
+        for row in (tau_row, tau_row + 1):
+            r = (nu_app(1, row, True) - ROWS[row][0]) / (nu_app(1, row, False) - ROWS[row][0])
+            assert abs(r - math.sqrt(2.0)) < 0.07, (row, r)
+    for diagonal in (False, True):
+        a, b = nu_app(1, 0, diagonal) - ROWS[0][0], nu_app(1, 2, diagonal) - ROWS[2][0]
+        assert abs(a - b) / a < 0.02, (diagonal, a, b)
 
 
 def spinodal(P, T, precision, steps, L=512, seed=1):

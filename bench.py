@@ -227,14 +227,13 @@ def run_server_bench(P, stream, njobs, step_scale):
     mean_work = work / njobs
     jobs = server_jobs(P, S, njobs, step_scale, rate_hz=1.2 * rate / mean_work)
     serial_jobs = server_jobs(P, S, njobs, step_scale, rate_hz=1.2 * rate / mean_work)
-    srv = S.SweepServer(mem_budget_bytes=int(64e9), stream=stream, chunk=100)
-    for j in jobs:
-        srv.submit(j)
-    st = srv.run()
+    with S.BatchServer(mem_budget_bytes=int(64e9), chunk=100) as srv:
+        st = S.run_jobs(srv, jobs)
     ss = S.run_serial(serial_jobs, stream)
     return {"jobs": njobs, "steps_scale": step_scale, "node_updates": work,
             "batched": {"glups": st.glups, "p50_s": st.pct(50), "p99_s": st.pct(99),
-                        "makespan_s": st.makespan},
+                        "makespan_s": st.makespan, "launches": st.launches,
+                        "server": "native lbm_batch_* (C++ worker thread)"},
             "serial": {"glups": ss.glups, "p50_s": ss.pct(50), "p99_s": ss.pct(99),
                        "makespan_s": ss.makespan}}
 

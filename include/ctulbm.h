@@ -206,6 +206,68 @@ int lbm_sync(lbm_handle* h);
 /* Number of steps taken since the last init / set. */
 int64_t lbm_step_count(const lbm_handle* h);
 
+/* ---- batch server -----------------------------------------------------------
+ * Continuous batching of many independent lattices (parameter sweeps over T,
+ * shear rate, rho_ext: no counterpart in the paper, which runs one lattice at
+ * a time).  A worker thread owned by the server admits submitted jobs in
+ * submission order while their device footprint fits max_bytes, advances all
+ * resident jobs together (one batched launch per step for FP32 lattices with
+ * the same scheme, lbm_step_many), records each job's diagnostics every
+ * diag_every steps and at its end, copies its final rho, u to host memory and
+ * frees its device memory at once.  Jobs run to completion; a job's result
+ * equals the one it has alone to FP32 rounding (exactly in FP64).
+ *
+ *   max_bytes   device memory the server may hold for jobs (each job needs
+ *               32 x sizeof(storage) + 24 bytes per node)
+ *   chunk_steps largest number of steps between two scheduling decisions
+ *   cuda_stream stream for all of the server's work (NULL: the server creates
+ *               its own); the device current at lbm_batch_create is used
+ * All lbm_batch_* calls are thread-safe.  Returns LBM_ERR_INVALID_ARG for a
+ * null argument, max_bytes = 0 or chunk_steps < 1, LBM_ERR_CUDA or
+ * LBM_ERR_OOM if the stream or thread cannot be made. */
+typedef struct lbm_batch lbm_batch;
+
+#define LBM_JOB_PENDING 0          /* submitted, waiting for device memory */
+#define LBM_JOB_ACTIVE 1           /* resident and stepping */
+#define LBM_JOB_DONE 2             /* finished; final fields held on the host until fetched */
+#define LBM_JOB_FAILED 3           /* error holds the cause (e.g. LBM_ERR_NONFINITE) */
+
+typedef struct lbm_job_result {
+  int32_t status;          /* LBM_JOB_* */
+  int32_t error;           /* LBM_OK or the code that failed the job */
+  int64_t steps_done, nsteps;
+  int64_t diag_step;       /* step of `diag` (-1: no record yet) */
+  double t_submit, t_start, t_finish;  /* seconds since lbm_batch_create (-1: not yet) */
+  lbm_diag diag;           /* last diagnostics record, as lbm_diagnostics (r_ring = 0) */
+} lbm_job_result;
+
+typedef struct lbm_batch_info {
+  int64_t pending, active, done, failed;
+  int64_t used_bytes;      /* device bytes held by resident jobs */
+  int64_t node_updates;    /* lattice nodes x steps advanced so far */
+  int64_t launches;        /* lbm_step_many calls made by the worker */
+} lbm_batch_info;
+
+int lbm_batch_create(size_t max_bytes, int32_t chunk_steps, void* cuda_stream, lbm_batch** out);
+/* Stops the worker after the step in flight, frees every job and the server. */
+void lbm_batch_destroy(lbm_batch* b);
+/* Queue a job.  rho, ux, uy: host FP64 [Ly][Lx], copied before return.
+ * nsteps >= 1; diag_every >= 0 (0: a record at the end only); threshold:
+ * bubble-site threshold of the records.  Returns the job id (>= 0) or
+ * LBM_ERR_INVALID_ARG / the code lbm_create would return for these params,
+ * LBM_ERR_OOM when the job alone exceeds max_bytes. */
+int64_t lbm_batch_submit(lbm_batch* b, const lbm_params* p, const double* rho, const double* ux,
+                         const double* uy, int64_t nsteps, int64_t diag_every, double threshold);
+/* Current state of a job (LBM_ERR_INVALID_ARG for an unknown id). */
+int lbm_batch_poll(lbm_batch* b, int64_t job, lbm_job_result* out);
+/* Block until the job is DONE or FAILED (job = -1: every submitted job) or
+ * timeout_s passes (< 0: no limit); LBM_ERR_TIMEOUT on timeout. */
+int lbm_batch_wait(lbm_batch* b, int64_t job, double timeout_s, lbm_job_result* out);
+/* Copy a DONE job's final rho, ux, uy (host FP64 [Ly][Lx], any may be NULL)
+ * and release them; later fetches return LBM_ERR_INVALID_ARG. */
+int lbm_batch_fetch(lbm_batch* b, int64_t job, double* rho, double* ux, double* uy);
+int lbm_batch_get_info(lbm_batch* b, lbm_batch_info* out);
+
 /* Launch geometry of the handle's fused step kernel (no counterpart in the
  * paper: for tuning, benchmarking and tests).
  *   grid          CTAs of the persistent launch (SMs x resident CTAs at most)

@@ -59,13 +59,28 @@ class lbm_diag(C.Structure):
     ]
 
 
+class lbm_job_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("error", C.c_int32), ("steps_done", C.c_int64),
+                ("nsteps", C.c_int64), ("diag_step", C.c_int64), ("t_submit", C.c_double),
+                ("t_start", C.c_double), ("t_finish", C.c_double), ("diag", lbm_diag)]
+
+
+class lbm_batch_info(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("pending", "active", "done", "failed", "used_bytes",
+                                         "node_updates", "launches")]
+
+
+LBM_JOB_PENDING, LBM_JOB_ACTIVE, LBM_JOB_DONE, LBM_JOB_FAILED = 0, 1, 2, 3
+
+
 _lib = None
 EXPORTS = ["lbm_default_params", "lbm_create", "lbm_destroy", "lbm_init_rho_u", "lbm_step_many",
            "lbm_step_diag",
            "lbm_init_rho_u_device", "lbm_set_f", "lbm_get_f", "lbm_set_f_device",
            "lbm_get_f_device", "lbm_step", "lbm_moments", "lbm_moments_device",
            "lbm_diagnostics", "lbm_histogram", "lbm_sync", "lbm_step_count", "lbm_strerror",
-           "lbm_get_kernel_info"]
+           "lbm_get_kernel_info", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_submit",
+           "lbm_batch_poll", "lbm_batch_wait", "lbm_batch_fetch", "lbm_batch_get_info"]
 
 
 def lib_path() -> str:
@@ -99,6 +114,16 @@ def lib():
         L.lbm_step_count.argtypes = [H]
         L.lbm_step_count.restype = i64
         L.lbm_get_kernel_info.argtypes = [H, P(lbm_kernel_info)]
+        B = C.c_void_p
+        L.lbm_batch_create.argtypes = [C.c_size_t, C.c_int32, vp, P(B)]
+        L.lbm_batch_destroy.argtypes = [B]
+        L.lbm_batch_destroy.restype = None
+        L.lbm_batch_submit.argtypes = [B, P(lbm_params), vp, vp, vp, i64, i64, C.c_double]
+        L.lbm_batch_submit.restype = i64
+        L.lbm_batch_poll.argtypes = [B, i64, P(lbm_job_result)]
+        L.lbm_batch_wait.argtypes = [B, i64, C.c_double, P(lbm_job_result)]
+        L.lbm_batch_fetch.argtypes = [B, i64, vp, vp, vp]
+        L.lbm_batch_get_info.argtypes = [B, P(lbm_batch_info)]
         L.lbm_histogram_noalloc.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double,
                                             C.c_int32, C.c_double, C.c_double, vp, P(C.c_int64)]
         L.lbm_strerror.argtypes = [C.c_int]

@@ -382,12 +382,19 @@ int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out) {
     return LBM_ERR_CUDA;
   }
   // work items: row blocks of up to 256 rows x strips; blocks shrink (down to
-  // 96 rows, where the 5-row warm-up still costs < 8 %) when a lattice would
-  // leave the grid with fewer than ~3 items per CTA
+  // 96 rows, where the 7-row pipeline warm-up still costs < 8 %) when a
+  // lattice would leave the grid with fewer than ~3 items per CTA.  A lattice
+  // too small to give every CTA one 96-row item is latency-bound: its blocks
+  // shrink further (down to 16 rows), trading warm-up work for a shorter row
+  // loop per CTA.
   const long long rows_total = (long long)h->nstrip * p->Ly;
   const long long grid_max = (long long)nsm * occ;
   long long rb = rows_total / (3 * grid_max);
   rb = rb < 96 ? 96 : (rb > 256 ? 256 : rb);
+  if (rows_total < 96 * grid_max) {
+    const long long fill = (rows_total + grid_max - 1) / grid_max;
+    rb = fill < 16 ? 16 : fill;
+  }
   h->row_block = (int)rb;
   const long long items = (long long)((p->Ly + rb - 1) / rb) * h->nstrip;
   h->grid = (int)(items < grid_max ? items : grid_max);
@@ -567,9 +574,16 @@ int lbm_step_many(lbm_handle* const* handles, int32_t count, int64_t n) {
     long long total = 0;
     b.count = ng;
     b.sched = h0->d_sched;
+    // lattices share the launch, so each keeps row blocks of at least 96 rows
+    // (its own may be shorter: sized to fill the GPU alone)
+    int rbs[MAXB];
+    long long its[MAXB];
     for (int i = 0; i < ng; ++i) {
+      const StepArgs<float>& a = group[i]->a32;
+      rbs[i] = a.row_block < 96 ? (a.Ly < 96 ? a.Ly : 96) : a.row_block;
+      its[i] = (long long)((a.Ly + rbs[i] - 1) / rbs[i]) * a.nstrip;
       b.item_start[i] = total;
-      total += group[i]->a32.items;
+      total += its[i];
     }
     b.item_start[ng] = total;
     const int g = (int)(total < grid_max ? total : grid_max);
@@ -577,6 +591,8 @@ int lbm_step_many(lbm_handle* const* handles, int32_t count, int64_t n) {
       for (int i = 0; i < ng; ++i) {
         lbm_handle* h = group[i];
         b.L[i] = h->a32;
+        b.L[i].row_block = rbs[i];
+        b.L[i].items = its[i];
         b.L[i].fin = static_cast<const float*>(h->f[h->cur]);
         b.L[i].fout = static_cast<float*>(h->f[1 - h->cur]);
       }

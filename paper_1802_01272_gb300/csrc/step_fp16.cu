@@ -22,9 +22,8 @@ void* select(int order, int lim, bool vec) {
 
 cudaError_t launch_step_f16(const StepArgs<float>& a, const RowMaps& maps, int order, int lim,
                             bool vec, int grid, size_t smem, cudaStream_t s) {
+  // the shared-memory attribute was set by step_occupancy_* when the handle was made
   void* fn = select(order, lim, vec);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   void* args[] = {const_cast<StepArgs<float>*>(&a), const_cast<RowMaps*>(&maps)};
   return cudaLaunchKernel(fn, dim3(grid), dim3(NT), args, smem, s);
 }

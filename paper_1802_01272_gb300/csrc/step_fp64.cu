@@ -21,9 +21,8 @@ void* select(int order, int lim, bool vec) {
 
 cudaError_t launch_step_f64(const StepArgs<double>& a, const RowMaps& maps, int order, int lim,
                             bool vec, int grid, size_t smem, cudaStream_t s) {
+  // the shared-memory attribute was set by step_occupancy_* when the handle was made
   void* fn = select(order, lim, vec);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   void* args[] = {const_cast<StepArgs<double>*>(&a), const_cast<RowMaps*>(&maps)};
   return cudaLaunchKernel(fn, dim3(grid), dim3(NT), args, smem, s);
 }

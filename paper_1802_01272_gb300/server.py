@@ -1,30 +1,29 @@
 """Continuous-batching sweep server for many CTU lattice Boltzmann jobs.
 
 Parameter sweeps (phase diagrams over T, shear-rate sweeps over the
-capillary number) are many independent lattices.  The server keeps every
-admitted job's lattice resident in device memory and advances all active
-jobs together: each tick is one `lbm_step_many` call, i.e. one fused launch
-per step covering every compatible lattice, so small lattices that could not
-fill the GPU alone share it.  Jobs that arrive while others run are admitted
-as soon as their device-memory footprint fits the budget, and a finished job
-releases its memory at once (continuous batching, not a queue).
+capillary number) are many independent lattices.  `BatchServer` wraps the
+library's native server (lbm_batch_* in include/ctulbm.h): a C++ worker
+thread admits jobs in submission order while their device footprint fits the
+budget, advances every resident job together (one batched launch per step,
+so small lattices that could not fill the GPU alone share it), records
+diagnostics, and frees a finished job's memory at once.  This module only
+marshals jobs in and results out; `run_jobs` replays an arrival process and
+`run_serial` is the one-job-at-a-time baseline.
 
 Each job's result is the one it would have alone, to FP32 rounding (the
 batched launch performs the same per-node operations), which the tests check.
-
-The scheduling loop runs on the calling thread (`run`), with arrivals given
-as timestamps; `submit` may also be called from other threads.
 """
 from __future__ import annotations
 
-import heapq
-import threading
+import ctypes as C
 import time
 from dataclasses import dataclass, field
 
 import numpy as np
 
-from .binding import LBM_FP64, Lattice, Params, step_many
+from .binding import (LBM_FP16_SHIFTED, LBM_FP64, LBM_JOB_DONE, LBM_JOB_FAILED, Lattice, LBMError,
+                      Params, _check, _host, _stream_ptr, lbm_batch_info, lbm_diag, lbm_job_result,
+                      lib)
 
 
 @dataclass
@@ -34,21 +33,24 @@ class Job:
     ux: np.ndarray
     uy: np.ndarray
     nsteps: int
-    arrival: float = 0.0            # seconds after the server starts
+    arrival: float = 0.0            # seconds after the start of run_jobs / run_serial
     diag_threshold: float | None = None
+    diag_every: int = 0             # 0: a diagnostics record at the end only
+    keep_rho: bool = False
     id: int = -1
-    # filled by the server
-    admitted: float | None = None
+    # filled in
+    submitted: float | None = None  # wall clock of the submission (run_jobs clock)
     finished: float | None = None
     diag: dict | None = None
     rho_out: np.ndarray | None = None
-    done_steps: int = 0
-    keep_rho: bool = False
+    status: int = -1
+    error: int = 0
 
     def footprint(self) -> int:
-        """Device bytes of the job: two ping-pong buffers of 16 planes."""
-        elem = 8 if self.params.precision == LBM_FP64 else 4
-        return 2 * 16 * elem * self.params.Lx * self.params.Ly + 3 * 8 * self.params.Lx * self.params.Ly
+        """Device bytes the server reserves for the job (as the library counts)."""
+        elem = {LBM_FP64: 8, LBM_FP16_SHIFTED: 2}.get(self.params.precision, 4)
+        n = self.params.Lx * self.params.Ly
+        return 32 * elem * n + 24 * n + 4096
 
     @property
     def node_updates(self) -> int:
@@ -64,6 +66,7 @@ class ServerStats:
     makespan: float
     node_updates: int
     latencies: list = field(default_factory=list)
+    launches: int = 0
 
     @property
     def glups(self) -> float:
@@ -73,86 +76,101 @@ class ServerStats:
         return float(np.percentile(self.latencies, q)) if self.latencies else float("nan")
 
 
-class SweepServer:
-    """Admits jobs by device-memory footprint and advances all active jobs in
-    batched launches of `chunk` steps (fewer when a job is about to finish)."""
+def _diag_dict(d: lbm_diag) -> dict:
+    return {n: getattr(d, n) for n, _ in lbm_diag._fields_}
 
-    def __init__(self, mem_budget_bytes: int, stream=None, chunk: int = 200,
-                 max_active: int = 64):
-        self.budget = int(mem_budget_bytes)
-        self.stream = stream
-        self.chunk = int(chunk)
-        self.max_active = int(max_active)
-        self._lock = threading.Lock()
-        self._pending: list = []     # heap of (arrival, id, job)
-        self._next_id = 0
-        self.active: list = []       # (job, lattice)
-        self.used = 0
-        self.finished: list = []
+
+class BatchServer:
+    """The library's continuous-batching server (lbm_batch_*)."""
+
+    def __init__(self, mem_budget_bytes: int, chunk: int = 100, stream=None):
+        self._b = C.c_void_p()
+        _check(lib().lbm_batch_create(int(mem_budget_bytes), int(chunk), _stream_ptr(stream),
+                                      C.byref(self._b)), "lbm_batch_create")
 
     def submit(self, job: Job) -> int:
-        if job.footprint() > self.budget:
-            raise ValueError(f"job needs {job.footprint()} B, above the budget {self.budget} B")
-        with self._lock:
-            job.id = self._next_id
-            self._next_id += 1
-            heapq.heappush(self._pending, (job.arrival, job.id, job))
+        shape = (job.params.Ly, job.params.Lx)
+        a = [_host(x, shape) for x in (job.rho, job.ux, job.uy)]
+        thr = job.diag_threshold if job.diag_threshold is not None else 0.0
+        jid = lib().lbm_batch_submit(self._b, C.byref(job.params.c()),
+                                     *[x.ctypes.data for x in a], int(job.nsteps),
+                                     int(job.diag_every), thr)
+        if jid < 0:
+            raise LBMError(int(jid), "lbm_batch_submit")
+        job.id = int(jid)
         return job.id
 
-    def _admit(self, now: float):
-        with self._lock:
-            while (self._pending and self._pending[0][0] <= now
-                   and len(self.active) < self.max_active
-                   and self.used + self._pending[0][2].footprint() <= self.budget):
-                _, _, job = heapq.heappop(self._pending)
-                L = Lattice(job.params, self.stream)
-                L.init_rho_u(job.rho, job.ux, job.uy)
-                job.admitted = now
-                self.used += job.footprint()
-                self.active.append((job, L))
+    def poll(self, job_id: int) -> lbm_job_result:
+        r = lbm_job_result()
+        _check(lib().lbm_batch_poll(self._b, job_id, C.byref(r)), "lbm_batch_poll")
+        return r
 
-    def _retire(self, now_fn):
-        keep = []
-        for job, L in self.active:
-            if job.done_steps >= job.nsteps:
-                if job.diag_threshold is not None:
-                    job.diag = L.diagnostics(job.diag_threshold)
-                if job.keep_rho:
-                    job.rho_out = L.moments()[0]
-                else:
-                    L.sync()
-                job.finished = now_fn()
-                self.used -= job.footprint()
-                L.close()
-                self.finished.append(job)
-            else:
-                keep.append((job, L))
-        self.active = keep
+    def wait(self, job_id: int = -1, timeout: float | None = None) -> None:
+        _check(lib().lbm_batch_wait(self._b, job_id, -1.0 if timeout is None else timeout, None),
+               "lbm_batch_wait")
 
-    def run(self, clock=time.perf_counter) -> ServerStats:
-        """Serve until every submitted job is finished; arrivals are relative
-        to the start of this call."""
-        t0 = clock()
-        now = lambda: clock() - t0
-        total = 0
-        while True:
-            self._admit(now())
-            if not self.active:
-                with self._lock:
-                    if not self._pending:
-                        break
-                    wait = self._pending[0][0] - now()
-                if wait > 0:
-                    time.sleep(min(wait, 0.01))
-                continue
-            k = min(self.chunk, min(j.nsteps - j.done_steps for j, _ in self.active))
-            step_many([L for _, L in self.active], k)
-            for j, _ in self.active:
-                j.done_steps += k
-                total += j.params.Lx * j.params.Ly * k
-            self._retire(now)
-        return ServerStats(makespan=now(), node_updates=total,
-                           latencies=[j.latency for j in self.finished])
+    def fetch(self, job: Job) -> None:
+        """Fill job.diag, job.status and (if job.keep_rho) job.rho_out from a
+        finished job; the server then drops the job's final fields."""
+        r = self.poll(job.id)
+        job.status, job.error = r.status, r.error
+        job.diag = _diag_dict(r.diag) if r.diag_step >= 0 else None
+        if r.status == LBM_JOB_DONE:
+            rho = np.empty((job.params.Ly, job.params.Lx)) if job.keep_rho else None
+            _check(lib().lbm_batch_fetch(self._b, job.id,
+                                         rho.ctypes.data if rho is not None else None, None, None),
+                   "lbm_batch_fetch")
+            job.rho_out = rho
+
+    def info(self) -> dict:
+        i = lbm_batch_info()
+        _check(lib().lbm_batch_get_info(self._b, C.byref(i)), "lbm_batch_get_info")
+        return {n: getattr(i, n) for n, _ in lbm_batch_info._fields_}
+
+    def close(self):
+        if self._b:
+            lib().lbm_batch_destroy(self._b)
+            self._b = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def run_jobs(server: BatchServer, jobs, clock=time.perf_counter) -> ServerStats:
+    """Submit each job at its arrival time (relative to this call), wait for
+    all, collect results.  Latency = finish - arrival, with the finish time
+    taken from the server's own record of the job's end."""
+    order = sorted(jobs, key=lambda j: j.arrival)
+    t0 = clock()
+    offsets = []
+    for j in order:
+        while clock() - t0 < j.arrival:
+            time.sleep(min(j.arrival - (clock() - t0), 0.005))
+        server.submit(j)
+        r = server.poll(j.id)
+        j.submitted = clock() - t0
+        offsets.append(j.submitted - r.t_submit)    # run_jobs clock - server clock
+    server.wait(-1)
+    makespan = clock() - t0
+    off = float(np.median(offsets))
+    for j in order:
+        r = server.poll(j.id)
+        j.finished = r.t_finish + off
+        server.fetch(j)
+        if j.status == LBM_JOB_FAILED:
+            raise LBMError(j.error, f"batch job {j.id}")
+    info = server.info()
+    return ServerStats(makespan=makespan, node_updates=sum(j.node_updates for j in order),
+                       latencies=[j.latency for j in order], launches=info["launches"])
 
 
 def run_serial(jobs, stream=None, clock=time.perf_counter) -> ServerStats:
@@ -163,12 +181,14 @@ def run_serial(jobs, stream=None, clock=time.perf_counter) -> ServerStats:
     lat = []
     for job in sorted(jobs, key=lambda j: j.arrival):
         while clock() - t0 < job.arrival:
-            time.sleep(min(job.arrival - (clock() - t0), 0.01))
+            time.sleep(min(job.arrival - (clock() - t0), 0.005))
         with Lattice(job.params, stream) as L:
             L.init_rho_u(job.rho, job.ux, job.uy)
             L.step(job.nsteps)
             if job.diag_threshold is not None:
                 job.diag = L.diagnostics(job.diag_threshold)
+            if job.keep_rho:
+                job.rho_out = L.moments()[0]
             else:
                 L.sync()
         job.finished = clock() - t0

@@ -96,3 +96,19 @@ def test_strerror(P):
     assert L.lbm_strerror(0) == b"success"
     assert b"CFL" in L.lbm_strerror(-2)
     assert L.lbm_strerror(-99) == b"unknown error"
+
+
+def test_batch_server_argument_checks(P):
+    """lbm_batch_* reject bad arguments before touching the GPU."""
+    import ctypes as C
+    from paper_1802_01272_gb300.binding import lbm_batch_info, lbm_job_result
+    L = P.lib()
+    b = C.c_void_p()
+    assert L.lbm_batch_create(0, 10, None, C.byref(b)) == -1
+    assert L.lbm_batch_create(1 << 20, 0, None, C.byref(b)) == -1
+    assert L.lbm_batch_create(1 << 20, 10, None, None) == -1
+    assert L.lbm_batch_poll(None, 0, C.byref(lbm_job_result())) == -1
+    assert L.lbm_batch_get_info(None, C.byref(lbm_batch_info())) == -1
+    assert L.lbm_batch_wait(None, -1, 0.0, None) == -1
+    assert L.lbm_batch_fetch(None, 0, None, None, None) == -1
+    L.lbm_batch_destroy(None)

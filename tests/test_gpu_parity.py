@@ -109,7 +109,7 @@ def test_kernel_info_staging_paths(P):
             k = L.kernel_info()
         assert k["tensor_copies"] == want, (Lx, Ly, prec, k)
         assert k["threads"] == 256 and k["strips"] == (Lx + 55) // 56 and k["grid"] >= 1
-        assert 96 <= k["row_block"] <= 256
+        assert 16 <= k["row_block"] <= 256
 
 
 def test_fp32_shifted_1000_steps(P, oracle_mod):

@@ -119,6 +119,63 @@ def test_table_III_ctu1_scaling():
         assert abs(a - b) / a < 0.02, (diagonal, a, b)
 
 
+def shear_wave_peaks(P, order, tau, diagonal, regularize, times, ds=1 / 128):
+    """u_perp(0, t) / U of a lambda = 2 shear wave (U = 0.01, rho = T = 1, F = 0)
+    at the given times: axial on 256 x 16 nodes, diagonal on 362 x 362."""
+    if diagonal:
+        L = int(round(2 * math.sqrt(2) / ds))
+        Lx = Ly = L
+        kx = ky = 2 * math.pi / (L * ds)
+    else:
+        Lx, Ly = int(round(2 / ds)), 16
+        kx, ky = 2 * math.pi / (Lx * ds), 0.0
+    lp = P.Params(Lx=Lx, Ly=Ly, a=0.0, b=0.0, kappa=0.0, T=1.0, tau=tau, dt=1e-4, ds=ds,
+                  ctu_order=order, regularize=int(regularize), precision=P.LBM_FP64,
+                  rho_ref=1.0)
+    rho, ux, uy = synth.shear_wave(Lx, Ly, ds, 0.01, kx, ky)
+    k = math.hypot(kx, ky)
+    ex, ey = -ky / k, kx / k
+    out, done = [], 0
+    with P.Lattice(lp) as L_:
+        L_.init_rho_u(rho, ux, uy)
+        for t in times:
+            n = int(round(t / 1e-4))
+            L_.step(n - done)
+            done = n
+            _, a, b = L_.moments()
+            out.append((a[0, 0] * ex + b[0, 0] * ey) / 0.01)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_regularisation_restores_isotropy_at_large_tau(order):
+    """Sec. II D (shear waves with and without Eq. ereg, lambda = 2): for tau > 0.1
+    the unregularised axial and diagonal waves decay differently and the
+    regularisation brings them together; for tau <= 0.1 it leaves the decay
+    unchanged.  As in the paper's comparison, the diagonal wave runs on the
+    lattice with spacing ds / sqrt 2 (512 x 512 nodes), where CTU1's numerical
+    viscosity equals the axial one's at ds = 1/128."""
+    import paper_1802_01272_gb300 as P
+    times = [0.05, 0.1, 0.2, 0.3, 0.5]
+    ds_d = 1 / (128 * math.sqrt(2))
+    out = {}
+    for tau in (0.05, 0.5):
+        for r in (False, True):
+            out[(tau, r)] = (shear_wave_peaks(P, order, tau, False, r, times),
+                             shear_wave_peaks(P, order, tau, True, r, times, ds=ds_d))
+    aniso = {k: float(np.abs(v[0] - v[1]).max()) for k, v in out.items()}
+    change = float(np.abs(out[(0.05, False)][0] - out[(0.05, True)][0]).max())
+    print(f"\nCTU{order}: |axial - diagonal| tau=0.5 no reg {aniso[(0.5, False)]:.3e} "
+          f"reg {aniso[(0.5, True)]:.3e}; tau=0.05 no reg {aniso[(0.05, False)]:.3e} "
+          f"reg {aniso[(0.05, True)]:.3e}; |reg - no reg| axial tau=0.05 {change:.3e}")
+    print("  tau=0.5 axial no reg", np.round(out[(0.5, False)][0], 5),
+          "diag", np.round(out[(0.5, False)][1], 5))
+    print("  tau=0.5 axial reg   ", np.round(out[(0.5, True)][0], 5),
+          "diag", np.round(out[(0.5, True)][1], 5))
+    assert aniso[(0.5, True)] < 0.3 * aniso[(0.5, False)]
+    assert change < 0.3 * aniso[(0.5, False)]
+
+
 def spinodal(P, T, precision, steps, L=512, seed=1):
     lp = P.Params(Lx=L, Ly=L, T=T, precision=precision, rho_ref=1.0)
     rho, ux, uy = synth.noisy_uniform(L, L, 1.0, 1e-2, seed=seed)

@@ -94,17 +94,22 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    if it was taken on the current kernel source; else None."""
+def ncu_record(workload):
+    """The committed ncu summary of the step kernel for this workload, if it was
+    taken on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     if not os.path.exists(path):
         return None
-    d = json.load(open(path))
-    e = d.get(workload)
+    e = json.load(open(path)).get(workload)
     if not e or e.get("kernel_source_hash") != kernel_source_hash():
         return None
-    return float(e["dram_bytes_per_launch"])
+    return e
+
+
+def ncu_traffic(workload):
+    """DRAM bytes per launch of the step kernel (committed ncu summary) or None."""
+    e = ncu_record(workload)
+    return None if e is None else float(e["dram_bytes_per_launch"])
 
 
 class ClockSampler:
@@ -338,6 +343,20 @@ def main():
     alg_bytes = 2 * 16 * elem * nodes
     achieved = alg_bytes / (ms_per_step * 1e-3) / 1e9
     traffic = ncu_traffic(args.workload)
+    # the step is bound by instruction issue: GB300 issues
+    # 4 warp-instructions per clock per SM; the instructions per node update
+    # come from the committed ncu capture of this kernel source
+    rec = ncu_record(args.workload)
+    issue_roof = None
+    if rec and rec.get("thread_instructions_per_node"):
+        nsm = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+        ipn = float(rec["thread_instructions_per_node"])
+        ach = ipn * value / world * 1e9 / 1e12
+        pk = nsm * 4 * 32 * mhz * 1e6 / 1e12
+        issue_roof = {"bound": "alu", "instructions_per_node": ipn, "achieved": ach, "peak": pk,
+                      "unit": "T thread-instructions/s", "frac": ach / pk,
+                      "peak_source": f"derived: {nsm} SMs x 4 issue slots x 32 lanes x {mhz:.0f} MHz"}
 
     # ---------------- end to end through the C ABI with pinned host buffers
     e2e = None
@@ -397,6 +416,7 @@ def main():
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                          if peak_kind == "measured" else "fallback 6.8 TB/s",
                          "algorithmic_bytes_per_launch": alg_bytes},
+            "issue_roofline": issue_roof,
             "gpu_launches": args.steps,
             "clocks": clk,
             "e2e": e2e,

@@ -343,7 +343,7 @@ def main():
     alg_bytes = 2 * 16 * elem * nodes
     achieved = alg_bytes / (ms_per_step * 1e-3) / 1e9
     traffic = ncu_traffic(args.workload)
-    # the step is bound by instruction issue: GB300 issues
+    # the step is bound by instruction issue, not HBM: GB300 issues
     # 4 warp-instructions per clock per SM; the instructions per node update
     # come from the committed ncu capture of this kernel source
     rec = ncu_record(args.workload)

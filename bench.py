@@ -267,6 +267,7 @@ def main():
     ap.add_argument("--workload", default="sheared-bubble-6144", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch geometry")
     ap.add_argument("--server", type=int, default=0, metavar="NJOBS",
                     help="also run the sweep-server comparison over NJOBS config-5 jobs")
     ap.add_argument("--server-step-scale", type=float, default=0.05)
@@ -319,6 +320,9 @@ def main():
     L = P.Lattice(p, stream)
     d_rho, d_ux, d_uy = (torch.from_numpy(x).cuda() for x in (rho, ux, uy))
     L.init_rho_u_device(d_rho, d_ux, d_uy)
+    # launch geometry from the library's autotuner (its trial steps are part of
+    # the untimed warm-up)
+    launch = L.tune(3) if not args.no_tune else L.kernel_info()
     L.step(args.warmup)
     L.sync()
     clocks = ClockSampler(local)
@@ -367,6 +371,8 @@ def main():
         hr, hx, hy = (t.numpy() for t in pin[:3])
         orho, oux, ouy = (t.numpy() for t in pin[3:])
         E = P.Lattice(p, stream)
+        if not args.no_tune:
+            E.tune(3)                    # untimed, like the warm-up
         thr = 0.5 * (w["rho_ext"] + w["rho_v"])
         E.init_rho_u(hr, hx, hy)
         E.step_diag(2, thr)
@@ -410,7 +416,8 @@ def main():
                                  if p.ctu_order == 2 else "CTU1", "T": p.T, "tau": p.tau,
                        "boundary": "shear walls" if w["walls"] else "periodic",
                        "l2": "inputs 2x%.2f GiB > L2, no flush" % (16 * elem * nodes / 2**30),
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "launch": {k: launch[k] for k in ("grid", "row_block", "tensor_copies")}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"

@@ -134,7 +134,9 @@ int lbm_get_f(lbm_handle* h, double* f);
 int lbm_set_f_device(lbm_handle* h, const double* f);
 int lbm_get_f_device(lbm_handle* h, double* f);
 
-/* Advance n >= 0 steps on the handle's stream (asynchronous; one fused kernel per step). */
+/* Advance n >= 0 steps on the handle's stream (asynchronous; one fused kernel
+ * per step).  From 32 steps on, whole blocks of 16 steps go out as one CUDA
+ * graph launch (built on first use per handle; the same kernels, in order). */
 int lbm_step(lbm_handle* h, int64_t n);
 
 /* Advance n >= 1 steps and return the diagnostics of the final state, reduced
@@ -283,6 +285,16 @@ typedef struct lbm_kernel_info {
   int32_t grid, threads, smem_bytes, strips, row_block, tensor_copies;
 } lbm_kernel_info;
 int lbm_get_kernel_info(const lbm_handle* h, lbm_kernel_info* out);
+
+/* Autotune the launch geometry of the handle's step kernel (no counterpart in
+ * the paper): times steps_per_trial steps for each candidate row-block height
+ * (16 .. 1024 rows, up to about twice Ly) and each number of resident CTAs
+ * per SM, then keeps the fastest.  The trial steps are real steps of the run
+ * (lbm_step_count grows by their number); the results of a step do not depend
+ * on the launch geometry.  `out` (may be NULL) receives the chosen geometry.
+ * Synchronises the handle's stream.  Returns LBM_ERR_INVALID_ARG for a null
+ * handle or steps_per_trial < 1, LBM_ERR_CUDA if a launch or event fails. */
+int lbm_tune(lbm_handle* h, int32_t steps_per_trial, lbm_kernel_info* out);
 
 /* Static description of a code. */
 const char* lbm_strerror(int code);

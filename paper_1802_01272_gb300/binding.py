@@ -80,7 +80,7 @@ EXPORTS = ["lbm_default_params", "lbm_create", "lbm_destroy", "lbm_init_rho_u", 
            "lbm_get_f_device", "lbm_step", "lbm_moments", "lbm_moments_device",
            "lbm_diagnostics", "lbm_histogram", "lbm_sync", "lbm_step_count", "lbm_strerror",
            "lbm_get_kernel_info", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_submit",
-           "lbm_batch_poll", "lbm_batch_wait", "lbm_batch_fetch", "lbm_batch_get_info"]
+           "lbm_batch_poll", "lbm_batch_wait", "lbm_batch_fetch", "lbm_batch_get_info", "lbm_tune"]
 
 
 def lib_path() -> str:
@@ -114,6 +114,7 @@ def lib():
         L.lbm_step_count.argtypes = [H]
         L.lbm_step_count.restype = i64
         L.lbm_get_kernel_info.argtypes = [H, P(lbm_kernel_info)]
+        L.lbm_tune.argtypes = [H, C.c_int32, P(lbm_kernel_info)]
         B = C.c_void_p
         L.lbm_batch_create.argtypes = [C.c_size_t, C.c_int32, vp, P(B)]
         L.lbm_batch_destroy.argtypes = [B]
@@ -332,6 +333,13 @@ class Lattice:
     @property
     def step_count(self) -> int:
         return lib().lbm_step_count(self._h)
+
+    def tune(self, steps_per_trial: int = 3) -> dict:
+        """lbm_tune: time each launch geometry for steps_per_trial real steps and
+        keep the fastest; returns the chosen geometry (as kernel_info)."""
+        k = lbm_kernel_info()
+        _check(lib().lbm_tune(self._h, int(steps_per_trial), C.byref(k)), "lbm_tune")
+        return {n: getattr(k, n) for n, _ in lbm_kernel_info._fields_}
 
     def kernel_info(self) -> dict:
         """Launch geometry of the step kernel (lbm_get_kernel_info)."""

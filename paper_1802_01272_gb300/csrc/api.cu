@@ -42,6 +42,9 @@ struct lbm_handle {
   StepArgs<float> a32;
   StepArgs<double> a64;
   RowMaps tmap[2];  // tensor maps of f[0], f[1] (RPI-row and 1-row boxes)
+  // CUDA graphs of GRAPH_STEPS consecutive steps starting from f[0] / f[1]
+  // (built on first use, rebuilt when the launch geometry changes)
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
   AuxArgs aux;
 };
 
@@ -426,6 +429,8 @@ int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out) {
 void lbm_destroy(lbm_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  for (auto& g : h->graph)
+    if (g) cudaGraphExecDestroy(g);
   cudaFree(h->f[0]);
   cudaFree(h->f[1]);
   cudaFree(h->d_err);
@@ -519,28 +524,174 @@ int lbm_get_f(lbm_handle* h, double* f) {
   return r;
 }
 
+namespace {
+
+constexpr int GRAPH_STEPS = 16;  // steps per graph launch (even: the buffers come back)
+
+// One step launch from f[c] to f[1 - c].
+cudaError_t launch_one(lbm_handle* h, int c, int lim) {
+  if (h->elem != 8) {
+    h->a32.fin = h->f[c];
+    h->a32.fout = h->f[1 - c];
+    return (h->elem == 4 ? launch_step_f32 : launch_step_f16)(
+        h->a32, h->tmap[c], h->p.ctu_order, lim, h->vec, h->grid, h->smem, h->stream);
+  }
+  h->a64.fin = static_cast<const double*>(h->f[c]);
+  h->a64.fout = static_cast<double*>(h->f[1 - c]);
+  return launch_step_f64(h->a64, h->tmap[c], h->p.ctu_order, lim, h->vec, h->grid, h->smem,
+                         h->stream);
+}
+
+// A graph of GRAPH_STEPS step kernels chained in order, starting from f[c]:
+// one graph launch replaces GRAPH_STEPS kernel launches (small lattices are
+// bound by launch overhead).  Built with explicit kernel nodes, so it works
+// on any stream, the legacy default stream included.  nullptr on failure.
+cudaGraphExec_t build_graph(lbm_handle* h, int c, int lim) {
+  const bool f32 = h->elem != 8;
+  void* fn = h->elem == 8   ? step_kernel_ptr_f64(h->p.ctu_order, lim, h->vec)
+             : h->elem == 4 ? step_kernel_ptr_f32(h->p.ctu_order, lim, h->vec)
+                            : step_kernel_ptr_f16(h->p.ctu_order, lim, h->vec);
+  cudaGraph_t g = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return nullptr;
+  cudaGraphNode_t prev = nullptr;
+  bool ok = true;
+  for (int s = 0; s < GRAPH_STEPS && ok; ++s) {
+    const int cc = (c + s) & 1;
+    StepArgs<float> a32 = h->a32;
+    StepArgs<double> a64 = h->a64;
+    a32.fin = h->f[cc];
+    a32.fout = h->f[1 - cc];
+    a64.fin = static_cast<const double*>(h->f[cc]);
+    a64.fout = static_cast<double*>(h->f[1 - cc]);
+    RowMaps maps = h->tmap[cc];
+    void* args[2] = {f32 ? static_cast<void*>(&a32) : static_cast<void*>(&a64), &maps};
+    cudaKernelNodeParams kp{};
+    kp.func = fn;
+    kp.gridDim = dim3(h->grid);
+    kp.blockDim = dim3(NT);
+    kp.sharedMemBytes = (unsigned)h->smem;
+    kp.kernelParams = args;  // copied into the node
+    cudaGraphNode_t node = nullptr;
+    ok = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp) ==
+         cudaSuccess;
+    prev = node;
+  }
+  cudaGraphExec_t ex = nullptr;
+  if (ok && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) ex = nullptr;
+  cudaGraphDestroy(g);
+  return ex;
+}
+
+void drop_graphs(lbm_handle* h) {
+  for (auto& g : h->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+}  // namespace
+
 int lbm_step(lbm_handle* h, int64_t n) {
   if (!h || n < 0) return LBM_ERR_INVALID_ARG;
   const int lim = h->p.ctu_order == 1 ? 0 : h->p.limiter;
-  for (int64_t s = 0; s < n; ++s) {
-    cudaError_t e;
-    if (h->elem != 8) {
-      h->a32.fin = h->f[h->cur];
-      h->a32.fout = h->f[1 - h->cur];
-      e = (h->elem == 4 ? launch_step_f32 : launch_step_f16)(h->a32, h->tmap[h->cur],
-                                                             h->p.ctu_order, lim, h->vec, h->grid,
-                                                             h->smem, h->stream);
-    } else {
-      h->a64.fin = static_cast<const double*>(h->f[h->cur]);
-      h->a64.fout = static_cast<double*>(h->f[1 - h->cur]);
-      e = launch_step_f64(h->a64, h->tmap[h->cur], h->p.ctu_order, lim, h->vec, h->grid, h->smem,
-                          h->stream);
+  // whole blocks of GRAPH_STEPS steps by graph launches when there are two or more
+  if (n >= 2 * GRAPH_STEPS) {
+    cudaGraphExec_t& g = h->graph[h->cur];
+    if (!g) g = build_graph(h, h->cur, lim);
+    if (g) {
+      for (; n >= GRAPH_STEPS; n -= GRAPH_STEPS) {
+        const cudaError_t e = cudaGraphLaunch(g, h->stream);
+        if (e != cudaSuccess) return cuda_check(h, e);
+        h->steps += GRAPH_STEPS;  // an even count: h->cur is unchanged
+      }
     }
+  }
+  for (int64_t s = 0; s < n; ++s) {
+    const cudaError_t e = launch_one(h, h->cur, lim);
     if (e != cudaSuccess) return cuda_check(h, e);
     h->cur ^= 1;
     h->steps += 1;
   }
   return LBM_OK;
+}
+
+int lbm_tune(lbm_handle* h, int32_t steps_per_trial, lbm_kernel_info* out) {
+  if (!h || steps_per_trial < 1) return LBM_ERR_INVALID_ARG;
+  const int lim = h->p.ctu_order == 1 ? 0 : h->p.limiter;
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+  const int occ = h->elem == 4   ? step_occupancy_f32(h->p.ctu_order, lim, h->vec, h->smem)
+                  : h->elem == 2 ? step_occupancy_f16(h->p.ctu_order, lim, h->vec, h->smem)
+                                 : step_occupancy_f64(h->p.ctu_order, lim, h->vec, h->smem);
+  if (nsm < 1 || occ < 1) return set_err(h, LBM_ERR_CUDA);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return set_err(h, LBM_ERR_CUDA);
+  }
+  auto apply = [&](int rb, int ctas) {
+    const long long items = (long long)((h->p.Ly + rb - 1) / rb) * h->nstrip;
+    const long long gmax = (long long)nsm * ctas;
+    h->row_block = rb;
+    h->grid = (int)(items < gmax ? items : gmax);
+    h->a32.row_block = h->a64.row_block = rb;
+    h->a32.items = h->a64.items = items;
+  };
+  // one trial: n real steps with geometry (rb, ctas), GPU time in ms
+  int r = LBM_OK;
+  auto trial = [&](int rb, int ctas, int n, float* ms) -> bool {
+    apply(rb, ctas);
+    cudaEventRecord(e0, h->stream);
+    for (int s = 0; s < n; ++s) {
+      const cudaError_t e = launch_one(h, h->cur, lim);
+      if (e != cudaSuccess) {
+        r = cuda_check(h, e);
+        return false;
+      }
+      h->cur ^= 1;
+      h->steps += 1;
+    }
+    cudaEventRecord(e1, h->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(ms, e0, e1) != cudaSuccess) {
+      r = set_err(h, LBM_ERR_CUDA);
+      return false;
+    }
+    return true;
+  };
+  const int cur_rb = h->row_block;
+  int cur_c = (int)((h->grid + nsm - 1) / nsm);
+  cur_c = cur_c < 1 ? 1 : (cur_c > occ ? occ : cur_c);
+  // the current geometry sets the trial length: at least ~1 ms of GPU time
+  float ms = 0.0f;
+  int steps = steps_per_trial;
+  if (trial(cur_rb, cur_c, steps_per_trial, &ms) && ms > 0.0f && ms < 1.0f) {
+    const float want = steps_per_trial / ms;
+    steps = want > 1000.0f ? 1000 : (int)want + 1;
+  }
+  float best = 0.0f;
+  int best_rb = cur_rb, best_c = cur_c;
+  if (r == LBM_OK && trial(cur_rb, cur_c, steps, &best)) {
+    const int rbs[] = {16, 32, 64, 96, 128, 192, 256, 384, 512, 1024};
+    for (int ctas = 1; ctas <= occ && r == LBM_OK; ++ctas) {
+      for (int rb : rbs) {
+        if (rb > 16 && rb >= 2 * h->p.Ly) break;  // one block covers the lattice already
+        if (rb == cur_rb && ctas == cur_c) continue;
+        if (!trial(rb, ctas, steps, &ms)) break;
+        if (ms < best) {
+          best = ms;
+          best_rb = rb;
+          best_c = ctas;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  apply(best_rb, best_c);
+  drop_graphs(h);  // built for the old geometry
+  if (out) lbm_get_kernel_info(h, out);
+  return r;
 }
 
 int lbm_step_many(lbm_handle* const* handles, int32_t count, int64_t n) {

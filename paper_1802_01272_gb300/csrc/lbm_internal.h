@@ -38,6 +38,11 @@ int step_batch_occupancy_f32(int order, int lim, bool vec, size_t smem);
 int step_occupancy_f32(int order, int lim, bool vec, size_t smem);
 int step_occupancy_f64(int order, int lim, bool vec, size_t smem);
 int step_occupancy_f16(int order, int lim, bool vec, size_t smem);
+// The step kernel a launch_step_* call would run (for CUDA graph kernel nodes,
+// whose parameters are (StepArgs, RowMaps) as in a direct launch).
+void* step_kernel_ptr_f32(int order, int lim, bool vec);
+void* step_kernel_ptr_f64(int order, int lim, bool vec);
+void* step_kernel_ptr_f16(int order, int lim, bool vec);
 
 // Dynamic shared memory of the step kernel: staging ring in the storage type
 // (stage_elem bytes per value), the other rings in the arithmetic type.

@@ -27,6 +27,8 @@ cudaError_t launch_step_f32(const StepArgs<float>& a, const RowMaps& maps, int o
   return cudaLaunchKernel(fn, dim3(grid), dim3(NT), args, smem, s);
 }
 
+void* step_kernel_ptr_f32(int order, int lim, bool vec) { return select(order, lim, vec); }
+
 int step_occupancy_f32(int order, int lim, bool vec, size_t smem) {
   void* fn = select(order, lim, vec);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=

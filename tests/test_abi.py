@@ -112,3 +112,4 @@ def test_batch_server_argument_checks(P):
     assert L.lbm_batch_wait(None, -1, 0.0, None) == -1
     assert L.lbm_batch_fetch(None, 0, None, None, None) == -1
     L.lbm_batch_destroy(None)
+    assert L.lbm_tune(None, 3, None) == -1

@@ -273,3 +273,43 @@ def test_step_diag_fused_record_matches_full_diagnostics(P):
         for n in ("a", "b", "D"):
             assert abs(d[n] - full[n]) < 1e-2 * max(1.0, abs(full[n]))
         assert np.isnan(d["rho_min"]) and not np.isnan(full["rho_min"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_graph_launched_steps_equal_single_launches(P, prec):
+    """lbm_step(n >= 32) sends blocks of 16 steps as one CUDA graph launch: the
+    same kernels in the same order, so the state is bit-identical to stepping
+    one launch at a time (from either buffer parity)."""
+    precision = P.LBM_FP64 if prec == "fp64" else P.LBM_FP32_SHIFTED
+    lp = P.Params(Lx=200, Ly=120, precision=precision, T=0.85, rho_ref=1.6, rho_ext=1.6,
+                  boundary=P.LBM_BC_SHEAR_WALLS, shear_rate=2 * 0.1 / (120 / 256.0))
+    rho, ux, uy = synth.bubble(200, 120, 1.6, 0.5, R=25, W=2)
+    with P.Lattice(lp) as A, P.Lattice(lp) as B:
+        A.init_rho_u(rho, ux, uy)
+        B.init_rho_u(rho, ux, uy)
+        A.step(1)
+        A.step(50)           # odd start parity, 3 graph launches + 2 single steps
+        A.step(40)           # even start parity
+        for _ in range(91):
+            B.step(1)
+        assert A.step_count == B.step_count == 91
+        assert np.array_equal(A.get_f(), B.get_f())
+
+
+def test_tune_picks_a_geometry_and_keeps_results(P):
+    """lbm_tune times launch geometries with real steps; the state after the
+    same number of steps is bit-identical to an untuned run (the arithmetic
+    of a node does not depend on how rows are split into work items)."""
+    for precision in (P.LBM_FP64, P.LBM_FP32_SHIFTED):
+        lp = P.Params(Lx=300, Ly=260, precision=precision, T=0.85, rho_ref=1.6)
+        rho, ux, uy = synth.noisy_uniform(300, 260, 1.6, 1e-2, seed=7)
+        with P.Lattice(lp) as A, P.Lattice(lp) as B:
+            A.init_rho_u(rho, ux, uy)
+            B.init_rho_u(rho, ux, uy)
+            k = A.tune(2)
+            n = A.step_count
+            assert n >= 2 * 4
+            assert k == A.kernel_info() and 16 <= k["row_block"] <= 1024
+            A.step(40)
+            B.step(n + 40)
+            assert np.array_equal(A.get_f(), B.get_f())

@@ -243,6 +243,32 @@ def run_server_bench(P, stream, njobs, step_scale):
                        "makespan_s": ss.makespan}}
 
 
+def make_sync(dist, device):
+    """The timing protocol's helpers for one rank: barrier() synchronises the
+    device on both sides of a process-group barrier (a no-op group of one when
+    dist is None); max_over_ranks(x) returns the largest x over all ranks."""
+    import torch
+
+    def sync():
+        if device.type == "cuda":
+            torch.cuda.synchronize(device)
+
+    def barrier():
+        sync()
+        if dist is not None:
+            dist.barrier()
+            sync()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    return barrier, max_over_ranks
+
+
 def run_reference(args, w, rank, world):
     if rank != 0:
         return
@@ -303,18 +329,7 @@ def main():
     nodes = p.Lx * p.Ly
     elem = {P.LBM_FP32_SHIFTED: 4, P.LBM_FP16_SHIFTED: 2}.get(p.precision, 8)
 
-    def barrier():
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-            torch.cuda.synchronize()
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier, max_over_ranks = make_sync(dist, torch.device("cuda", local))
 
     # ---------------- device-resident throughput
     L = P.Lattice(p, stream)

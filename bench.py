@@ -340,6 +340,9 @@ def main():
     launch = L.tune(3) if not args.no_tune else L.kernel_info()
     L.step(args.warmup)
     L.sync()
+    # measured compute peaks for the issue and FP32 rooflines (untimed)
+    from paper_1802_01272_gb300.binding import measure_peaks
+    peaks = measure_peaks(stream)
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
@@ -366,16 +369,27 @@ def main():
     # 4 warp-instructions per clock per SM; the instructions per node update
     # come from the committed ncu capture of this kernel source
     rec = ncu_record(args.workload)
-    issue_roof = None
+    issue_roof = fp32_roof = None
     if rec and rec.get("thread_instructions_per_node"):
         nsm = torch.cuda.get_device_properties(local).multi_processor_count
         mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
         ipn = float(rec["thread_instructions_per_node"])
         ach = ipn * value / world * 1e9 / 1e12
-        pk = nsm * 4 * 32 * mhz * 1e6 / 1e12
+        derived = nsm * 4 * 32 * mhz * 1e6 / 1e12
+        pk = peaks["issue_rate"] * 32 / 1e12 if peaks else derived
         issue_roof = {"bound": "alu", "instructions_per_node": ipn, "achieved": ach, "peak": pk,
                       "unit": "T thread-instructions/s", "frac": ach / pk,
-                      "peak_source": f"derived: {nsm} SMs x 4 issue slots x 32 lanes x {mhz:.0f} MHz"}
+                      "peak_source": "measured (lbm_measure_peaks: FP32 min3 + add chains)"
+                      if peaks else "derived", "peak_derived":
+                      derived, "peak_derived_source":
+                      f"{nsm} SMs x 4 issue slots x 32 lanes x {mhz:.0f} MHz"}
+    if rec and rec.get("fp32_flops_per_node") and peaks:
+        fpn = float(rec["fp32_flops_per_node"])
+        ach = fpn * value / world * 1e9 / 1e12
+        pk = peaks["fp32_flops"] / 1e12
+        fp32_roof = {"bound": "fp32", "flops_per_node": fpn, "achieved": ach, "peak": pk,
+                     "unit": "TFLOP/s", "frac": ach / pk,
+                     "peak_source": "measured (lbm_measure_peaks: FFMA chains)"}
 
     # ---------------- end to end through the C ABI with pinned host buffers
     e2e = None
@@ -439,6 +453,7 @@ def main():
                          if peak_kind == "measured" else "fallback 6.8 TB/s",
                          "algorithmic_bytes_per_launch": alg_bytes},
             "issue_roofline": issue_roof,
+            "fp32_roofline": fp32_roof,
             "gpu_launches": args.steps,
             "clocks": clk,
             "e2e": e2e,

@@ -296,6 +296,18 @@ int lbm_get_kernel_info(const lbm_handle* h, lbm_kernel_info* out);
  * handle or steps_per_trial < 1, LBM_ERR_CUDA if a launch or event fails. */
 int lbm_tune(lbm_handle* h, int32_t steps_per_trial, lbm_kernel_info* out);
 
+/* Measured compute peaks of the current device (no counterpart in the paper:
+ * the denominators of the compute rooflines a benchmark reports beside the
+ * HBM one).  Runs two short probe kernels on cuda_stream (NULL: the legacy
+ * default stream) and synchronises it:
+ *   fp32_flops : FP32 FMA throughput, flop/s (independent FFMA chains)
+ *   issue_rate : warp-instructions issued per second over the whole GPU, with
+ *                independent chains alternating a 3-input FP32 min and an
+ *                FP32 add (the ALU and FMA pipes the step kernel uses most)
+ * Allocates and frees a probe buffer of (SMs x 2048) floats.  Returns
+ * LBM_ERR_INVALID_ARG for a null output, LBM_ERR_OOM or LBM_ERR_CUDA. */
+int lbm_measure_peaks(void* cuda_stream, double* fp32_flops, double* issue_rate);
+
 /* Static description of a code. */
 const char* lbm_strerror(int code);
 

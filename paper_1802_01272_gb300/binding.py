@@ -80,7 +80,8 @@ EXPORTS = ["lbm_default_params", "lbm_create", "lbm_destroy", "lbm_init_rho_u", 
            "lbm_get_f_device", "lbm_step", "lbm_moments", "lbm_moments_device",
            "lbm_diagnostics", "lbm_histogram", "lbm_sync", "lbm_step_count", "lbm_strerror",
            "lbm_get_kernel_info", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_submit",
-           "lbm_batch_poll", "lbm_batch_wait", "lbm_batch_fetch", "lbm_batch_get_info", "lbm_tune"]
+           "lbm_batch_poll", "lbm_batch_wait", "lbm_batch_fetch", "lbm_batch_get_info", "lbm_tune",
+           "lbm_measure_peaks"]
 
 
 def lib_path() -> str:
@@ -115,6 +116,7 @@ def lib():
         L.lbm_step_count.restype = i64
         L.lbm_get_kernel_info.argtypes = [H, P(lbm_kernel_info)]
         L.lbm_tune.argtypes = [H, C.c_int32, P(lbm_kernel_info)]
+        L.lbm_measure_peaks.argtypes = [vp, d, d]
         B = C.c_void_p
         L.lbm_batch_create.argtypes = [C.c_size_t, C.c_int32, vp, P(B)]
         L.lbm_batch_destroy.argtypes = [B]
@@ -212,6 +214,15 @@ def step_many(lattices, n: int):
 
 
 NOALLOC_MAX_BINS = 4096
+
+
+def measure_peaks(stream=None) -> dict:
+    """lbm_measure_peaks: measured FP32 flop/s and warp-instruction issue rate
+    of the current device."""
+    f, i = C.c_double(), C.c_double()
+    _check(lib().lbm_measure_peaks(_stream_ptr(stream), C.byref(f), C.byref(i)),
+           "lbm_measure_peaks")
+    return {"fp32_flops": f.value, "issue_rate": i.value}
 
 
 def histogram_noalloc(f, precision: int, rho_ref: float, nbins: int, lo: float, hi: float,

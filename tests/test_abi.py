@@ -113,3 +113,4 @@ def test_batch_server_argument_checks(P):
     assert L.lbm_batch_fetch(None, 0, None, None, None) == -1
     L.lbm_batch_destroy(None)
     assert L.lbm_tune(None, 3, None) == -1
+    assert L.lbm_measure_peaks(None, None, None) == -1

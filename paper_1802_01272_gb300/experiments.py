@@ -5,7 +5,10 @@
 * the critical radius of Eq. (raggio_c) and the growth or collapse of bubbles
   around it with the density reservoir of Sec. III A;
 * bubble growth against the two-dimensional Rayleigh-Plesset equation
-  (Eq. rp), fed with the pressures measured on the lattice as in Sec. III B.
+  (Eq. rp), fed with the pressures measured on the lattice as in Sec. III B;
+* a bubble deformed by the shear between moving walls (Sec. III C): shape
+  from the gyration tensor (Eq. gyr), deformation D = (a - b)/(a + b), tilt
+  angle and capillary number Ca = mu_L gamma_dot R / sigma over time.
 
 Host-side analysis is FP64 numpy; every lattice step, moment and diagnostic
 runs in the library.  Lengths are in the paper's units (node spacing ds).
@@ -18,7 +21,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import eos
-from .binding import LBM_FP32_SHIFTED, LBM_FP64, Lattice, Params
+from .binding import LBM_BC_SHEAR_WALLS, LBM_FP32_SHIFTED, LBM_FP64, Lattice, Params
 
 
 def free_energy(rho, T, a=9 / 8, b=1 / 3):
@@ -164,3 +167,51 @@ def rp_prediction(run: BubbleRun, t0: float, sigma=None, window=0.5):
     R = rayleigh_plesset(R0, V0, ts, lambda t: np.interp(t, ts, pb),
                          lambda t: np.interp(t, ts, pf), run.r_inf, sigma, rl, rl * p.T * p.tau)
     return run.t[i0:], R
+
+
+@dataclass
+class ShearRun:
+    t: np.ndarray        # time
+    D: np.ndarray        # (a - b)/(a + b) from the gyration tensor
+    theta: np.ndarray    # tilt of the major axis to the flow direction x
+    R: np.ndarray        # mean radius (a + b)/2, lattice units of length
+    Ca: np.ndarray       # mu_L gamma_dot R / sigma
+    shear_rate: float
+
+
+def sheared_bubble(R0_nodes, capillary, Lx=1024, Ly=512, T=0.8, kappa=1e-4, ds=1 / 256,
+                   tau=1e-2, rho_ext=1.90, t_end=10.0, every=0.5,
+                   precision=LBM_FP32_SHIFTED, stream=None) -> ShearRun:
+    """Sec. III C: a vapour bubble (radius R0) growing in a superheated liquid
+    (rho_ext, 1.90 as in the paper's runs at T = 0.8, tau = 1e-2) sheared
+    between walls moving at -+u_w (y = 0, Ly), periodic in x.  The shear rate
+    is set from the target capillary number of the initial radius,
+    gamma_dot = Ca sigma / (mu_L R0) with mu_L = rho_L T tau; the fluid starts
+    in the linear shear profile.  Records the shape of Eq. (gyr) over time;
+    Ca(t) follows the growing mean radius, as in the paper."""
+    rl, rv = eos.coexistence(T)
+    sigma = eos.interface_tension(T, kappa)
+    mu_l = rl * T * tau
+    gdot = capillary * sigma / (mu_l * R0_nodes * ds)
+    uw = gdot * Ly * ds / 2.0
+    rho, ux, uy = bubble_fields(Lx, Ly, R0_nodes, rv, rho_ext, 2.0)
+    y = np.arange(Ly, dtype=np.float64)
+    ux = np.repeat((-uw + 2.0 * uw * (y + 1.0) / (Ly + 1.0))[:, None], Lx, axis=1)
+    p = _params(Lx, Ly, T, tau, kappa, ds, precision, rho_ext, boundary=LBM_BC_SHEAR_WALLS,
+                shear_rate=gdot, rho_ext=rho_ext)
+    thr = 0.5 * (rl + rv)
+    n_every = max(1, int(round(every / p.dt)))
+    t, D, th, R = [], [], [], []
+    with Lattice(p, stream) as L:
+        L.init_rho_u(rho, ux, uy)
+        for i in range(int(round(t_end / every)) + 1):
+            if i:
+                L.step(n_every)
+            d = L.diagnostics(thr)
+            t.append(i * n_every * p.dt)
+            D.append(d["D"])
+            th.append(d["theta"])
+            R.append(0.5 * (d["a"] + d["b"]) * ds)
+    R = np.array(R)
+    return ShearRun(t=np.array(t), D=np.array(D), theta=np.array(th), R=R,
+                    Ca=mu_l * gdot * R / sigma, shear_rate=gdot)

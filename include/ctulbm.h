@@ -212,11 +212,13 @@ int64_t lbm_step_count(const lbm_handle* h);
  * Continuous batching of many independent lattices (parameter sweeps over T,
  * shear rate, rho_ext: no counterpart in the paper, which runs one lattice at
  * a time).  A worker thread owned by the server admits submitted jobs in
- * submission order while their device footprint fits max_bytes, advances all
+ * submission order while their device footprint fits max_bytes and advances
  * resident jobs together (one batched launch per step for FP32 lattices with
- * the same scheme, lbm_step_many), records each job's diagnostics every
- * diag_every steps and at its end, copies its final rho, u to host memory and
- * frees its device memory at once.  Jobs run to completion; a job's result
+ * the same scheme, lbm_step_many): each tick the jobs with the least work
+ * left, as many as fill the GPU, while the others wait resident (short jobs
+ * are not slowed to the pace of the largest lattice); it records each job's
+ * diagnostics every diag_every steps and at its end, copies its final rho, u
+ * to host memory and frees its device memory at once.  Jobs run to completion; a job's result
  * equals the one it has alone to FP32 rounding (exactly in FP64).
  *
  *   max_bytes   device memory the server may hold for jobs (each job needs

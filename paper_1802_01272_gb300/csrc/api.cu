@@ -711,6 +711,10 @@ int lbm_step_many(lbm_handle* const* handles, int32_t count, int64_t n) {
   int ng = 0;
   auto flush = [&](int64_t steps) -> int {
     if (ng == 0) return LBM_OK;
+    if (ng == 1) {  // a lattice alone: the single-lattice path (graph launches, small parameters)
+      ng = 0;
+      return lbm_step(group[0], steps);
+    }
     int grid_max = 0;
     {
       int occ = step_batch_occupancy_f32(h0->p.ctu_order, lim0, true, group[0]->smem);

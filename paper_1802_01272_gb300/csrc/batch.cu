@@ -2,6 +2,7 @@
 // lbm_batch_* calls of include/ctulbm.h).  Host code only: it is a client of
 // the single-lattice C ABI (lbm_create, lbm_init_rho_u, lbm_step_many,
 // lbm_diagnostics, lbm_moments, lbm_destroy) driven by one worker thread.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -43,6 +44,7 @@ size_t footprint(const lbm_params& p) {
 struct lbm_batch {
   size_t max_bytes = 0;
   int chunk = 1;
+  long long fill_nodes = 0;  // lattice nodes per launch that keep every SM busy
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -115,9 +117,28 @@ void lbm_batch::run() {
       cv.notify_all();
     }
     if (active.empty()) continue;
+    // shortest remaining work first: advance the resident jobs with the fewest
+    // node-steps left, just enough of them to fill the GPU; the others stay
+    // resident and wait (short jobs finish early instead of crawling at the
+    // pace of the largest lattice in the batch)
+    std::vector<Job*> order(active), run, idle;
+    auto left_work = [](const Job* j) {
+      return (double)(j->nsteps - j->r.steps_done) * j->p.Lx * j->p.Ly;
+    };
+    std::stable_sort(order.begin(), order.end(),
+                     [&](const Job* a, const Job* b) { return left_work(a) < left_work(b); });
+    long long nodes = 0;
+    for (Job* j : order) {
+      if (!run.empty() && nodes >= fill_nodes)
+        idle.push_back(j);
+      else {
+        run.push_back(j);
+        nodes += (long long)j->p.Lx * j->p.Ly;
+      }
+    }
     // steps until the next event (a diagnostics record or a job's end)
     int64_t k = chunk;
-    for (Job* j : active) {
+    for (Job* j : run) {
       const int64_t left = j->nsteps - j->r.steps_done;
       k = left < k ? left : k;
       if (j->diag_every > 0) {
@@ -126,11 +147,11 @@ void lbm_batch::run() {
       }
     }
     std::vector<lbm_handle*> hs;
-    for (Job* j : active) hs.push_back(j->h);
+    for (Job* j : run) hs.push_back(j->h);
     const int e = lbm_step_many(hs.data(), (int32_t)hs.size(), k);
-    std::vector<Job*> keep;
+    std::vector<Job*> keep(idle);
     std::vector<std::pair<Job*, int>> ended;
-    for (Job* j : active) {
+    for (Job* j : run) {
       if (e != LBM_OK) {
         ended.emplace_back(j, e);
         continue;
@@ -183,6 +204,11 @@ int lbm_batch_create(size_t max_bytes, int32_t chunk_steps, void* cuda_stream, l
   b->chunk = chunk_steps;
   b->t0 = Clock::now();
   if (cudaGetDevice(&b->device) != cudaSuccess) return LBM_ERR_CUDA;
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
+    return LBM_ERR_CUDA;
+  // two resident CTAs per SM, two work items of 96 rows x 56 columns each
+  b->fill_nodes = (long long)nsm * 2 * 2 * 96 * 56;
   b->stream = static_cast<cudaStream_t>(cuda_stream);
   if (!b->stream) {
     if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)

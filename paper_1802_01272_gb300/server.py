@@ -4,9 +4,10 @@ Parameter sweeps (phase diagrams over T, shear-rate sweeps over the
 capillary number) are many independent lattices.  `BatchServer` wraps the
 library's native server (lbm_batch_* in include/ctulbm.h): a C++ worker
 thread admits jobs in submission order while their device footprint fits the
-budget, advances every resident job together (one batched launch per step,
-so small lattices that could not fill the GPU alone share it), records
-diagnostics, and frees a finished job's memory at once.  This module only
+budget, advances resident jobs together (one batched launch per step, so
+small lattices that could not fill the GPU alone share it; each tick the jobs
+with the least work left, as many as fill the GPU), records diagnostics, and
+frees a finished job's memory at once.  This module only
 marshals jobs in and results out; `run_jobs` replays an arrival process and
 `run_serial` is the one-job-at-a-time baseline.
 

@@ -102,3 +102,19 @@ def test_sheared_bubble_deformation_and_tilt():
     assert lo.theta[-1] < lo.theta[2] and hi.theta[-1] < lo.theta[-1]
     assert lo.R[-1] > 2.5 * lo.R[0]
     assert abs(hi.R[-1] - lo.R[-1]) / lo.R[-1] < 0.1
+
+
+def test_config3_quiescent_bubble_grows_in_superheated_liquid():
+    """Config 3 of the quiescent-growth experiments (Sec. III B at T = 0.9):
+    a tanh seed of radius 20 nodes at the Maxwell vapour density in liquid
+    held at rho_ext = 1.58 (Eq. raggio_c: R_c = 11.8 nodes) grows without
+    stopping, and the reservoir keeps the far field at rho_ext.  2048^2
+    nodes, tau = 1e-3, t = 3 (30000 steps)."""
+    from paper_1802_01272_gb300 import eos
+    from paper_1802_01272_gb300 import experiments as X
+    rc = X.critical_radius(0.9, 1.58, eos.interface_tension(0.9, 1e-4)) * 256
+    assert rc < 15.0
+    run = X.bubble_in_reservoir(20, 1.58, T=0.9, L=2048, tau=1e-3, t_end=3.0, every=0.5)
+    print("\nR nodes", np.round(run.R * 256, 2), " rho_inf", np.round(run.rho_inf, 4))
+    assert np.all(np.diff(run.R[1:]) > 0) and run.R[-1] > 3.5 * run.R[0]
+    assert np.abs(run.rho_inf - 1.58).max() < 2e-3

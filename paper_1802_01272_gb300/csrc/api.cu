@@ -33,7 +33,6 @@ struct lbm_handle {
   int64_t steps = 0;
   int sticky = LBM_OK;
   int grid = 0;
-  long long rows_per_cta = 0;
   int nstrip = 0;
   int row_block = 256;
   bool vec = false;
@@ -144,8 +143,6 @@ void fill_step_args(lbm_handle* h, StepArgs<T>& a) {
   a.Ly = p.Ly;
   a.plane = (long long)p.Lx * p.Ly;
   a.nstrip = h->nstrip;
-  a.rows_total = (long long)h->nstrip * p.Ly;
-  a.rows_per_cta = h->rows_per_cta;
   a.row_block = h->row_block;
   a.items = (long long)((p.Ly + h->row_block - 1) / h->row_block) * h->nstrip;
   a.sched = h->d_sched;
@@ -401,7 +398,6 @@ int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out) {
   h->row_block = (int)rb;
   const long long items = (long long)((p->Ly + rb - 1) / rb) * h->nstrip;
   h->grid = (int)(items < grid_max ? items : grid_max);
-  h->rows_per_cta = 0;
   if (h->elem == 8)
     fill_step_args<double>(h, h->a64);
   else

@@ -77,8 +77,6 @@ struct StepArgs {
   int Lx, Ly;
   long long plane;          // Lx * Ly
   int nstrip;
-  long long rows_total;     // nstrip * Ly
-  long long rows_per_cta;
   int row_block;            // rows per work item
   long long items;          // work items: ceil(Ly / row_block) * nstrip, row-block major
   unsigned long long* sched;  // [2]: next item, CTAs done (reset by the last CTA)
@@ -179,30 +177,6 @@ __device__ __forceinline__ int wrapi(int i, int n) {
   return r < 0 ? r + n : r;
 }
 
-template <typename T>
-__device__ __forceinline__ void load4(const T* p, T* v);
-template <>
-__device__ __forceinline__ void load4<float>(const float* p, float* v) {
-  float4 t = __ldg(reinterpret_cast<const float4*>(p));
-  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-}
-template <>
-__device__ __forceinline__ void load4<double>(const double* p, double* v) {
-  double2 t0 = __ldg(reinterpret_cast<const double2*>(p));
-  double2 t1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
-  v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
-}
-template <typename T>
-__device__ __forceinline__ void store4(T* p, const T* v);
-template <>
-__device__ __forceinline__ void store4<float>(float* p, const float* v) {
-  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-}
-template <>
-__device__ __forceinline__ void store4<double>(double* p, const double* v) {
-  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
-  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
-}
 template <typename T>
 __device__ __forceinline__ void sload4(const T* p, T* v) {
   if constexpr (sizeof(T) == 4) {

@@ -188,6 +188,18 @@ def cpu_baseline(w, seconds=15.0):
                       f"{dt:.1f} s"}
 
 
+def cpu_baseline_single_thread(workload, seconds=5.0):
+    """The same oracle sample on one host thread (a child process started
+    with OMP_NUM_THREADS=1, since the oracle's thread count is fixed at load)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--workload", workload,
+                          "--cpu-baseline-only", str(seconds)], env=env, capture_output=True,
+                         text=True, timeout=600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
 def server_jobs(P, S, njobs, step_scale, seed=4, rate_hz=None):
     """Config 5's job mix: lattices L^2, L in {256, 512, 1024, 2048}; T ~ U[0.75, 0.98];
     shear rate from Ca ~ U[0, 0.4] (Ca = mu_L gamma_dot R / sigma with the seed
@@ -294,6 +306,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch geometry")
+    ap.add_argument("--cpu-baseline-only", type=float, default=None, metavar="SECONDS",
+                    help="print the oracle's host-core sample for this workload and exit")
     ap.add_argument("--server", type=int, default=0, metavar="NJOBS",
                     help="also run the sweep-server comparison over NJOBS config-5 jobs")
     ap.add_argument("--server-step-scale", type=float, default=0.05)
@@ -301,6 +315,9 @@ def main():
     ap.add_argument("--limiter", type=int, default=None, help="override the limiter (profiling)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
+    if args.cpu_baseline_only is not None:
+        print(json.dumps(cpu_baseline(w, seconds=args.cpu_baseline_only)), flush=True)
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -430,6 +447,8 @@ def main():
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(w)
+        one = cpu_baseline_single_thread(args.workload)
+        cb["single_thread"] = {"value": one["value"], "cores": 1, "sample": one["sample"]}
 
     if rank == 0:
         line = {

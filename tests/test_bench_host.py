@@ -72,3 +72,10 @@ def test_reference_arm_prints_one_json_line():
                           "--warmup", "0"], cwd=ROOT, env=env, capture_output=True, text=True,
                          timeout=120)
     assert out.returncode == 0 and out.stdout.strip() == ""
+
+
+def test_single_thread_oracle_sample():
+    sys.path.insert(0, ROOT)
+    import bench
+    one = bench.cpu_baseline_single_thread("sheared-bubble-2048", seconds=1.0)
+    assert one["kind"] == "oracle" and one["cores"] == 1 and one["value"] > 0

@@ -306,6 +306,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch geometry")
+    ap.add_argument("--row-block", type=int, default=0,
+                    help="fix the row-block height (2 CTAs per SM) instead of tuning")
     ap.add_argument("--cpu-baseline-only", type=float, default=None, metavar="SECONDS",
                     help="print the oracle's host-core sample for this workload and exit")
     ap.add_argument("--server", type=int, default=0, metavar="NJOBS",
@@ -354,7 +356,10 @@ def main():
     L.init_rho_u_device(d_rho, d_ux, d_uy)
     # launch geometry from the library's autotuner (its trial steps are part of
     # the untimed warm-up)
-    launch = L.tune(3) if not args.no_tune else L.kernel_info()
+    if args.row_block:
+        launch = L.set_launch(args.row_block, 2)
+    else:
+        launch = L.tune(3) if not args.no_tune else L.kernel_info()
     L.step(args.warmup)
     L.sync()
     # measured compute peaks for the issue and FP32 rooflines (untimed)
@@ -417,7 +422,9 @@ def main():
         hr, hx, hy = (t.numpy() for t in pin[:3])
         orho, oux, ouy = (t.numpy() for t in pin[3:])
         E = P.Lattice(p, stream)
-        if not args.no_tune:
+        if args.row_block:
+            E.set_launch(args.row_block, 2)
+        elif not args.no_tune:
             E.tune(3)                    # untimed, like the warm-up
         thr = 0.5 * (w["rho_ext"] + w["rho_v"])
         E.init_rho_u(hr, hx, hy)

@@ -298,6 +298,14 @@ int lbm_get_kernel_info(const lbm_handle* h, lbm_kernel_info* out);
  * handle or steps_per_trial < 1, LBM_ERR_CUDA if a launch or event fails. */
 int lbm_tune(lbm_handle* h, int32_t steps_per_trial, lbm_kernel_info* out);
 
+/* Set the launch geometry explicitly (e.g. one that lbm_tune chose earlier for
+ * the same lattice size): row blocks of row_block rows, at most ctas_per_sm
+ * resident CTAs per SM.  Results do not depend on it.  No counterpart in the
+ * paper.  Returns LBM_ERR_INVALID_ARG for a null handle, row_block < 1 or
+ * ctas_per_sm < 1 or above what the kernel's resources allow on this device;
+ * LBM_ERR_CUDA if the device cannot be queried. */
+int lbm_set_launch(lbm_handle* h, int32_t row_block, int32_t ctas_per_sm);
+
 /* Measured compute peaks of the current device (no counterpart in the paper:
  * the denominators of the compute rooflines a benchmark reports beside the
  * HBM one).  Runs two short probe kernels on cuda_stream (NULL: the legacy

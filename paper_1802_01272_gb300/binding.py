@@ -81,7 +81,7 @@ EXPORTS = ["lbm_default_params", "lbm_create", "lbm_destroy", "lbm_init_rho_u", 
            "lbm_diagnostics", "lbm_histogram", "lbm_sync", "lbm_step_count", "lbm_strerror",
            "lbm_get_kernel_info", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_submit",
            "lbm_batch_poll", "lbm_batch_wait", "lbm_batch_fetch", "lbm_batch_get_info", "lbm_tune",
-           "lbm_measure_peaks"]
+           "lbm_measure_peaks", "lbm_set_launch"]
 
 
 def lib_path() -> str:
@@ -116,6 +116,7 @@ def lib():
         L.lbm_step_count.restype = i64
         L.lbm_get_kernel_info.argtypes = [H, P(lbm_kernel_info)]
         L.lbm_tune.argtypes = [H, C.c_int32, P(lbm_kernel_info)]
+        L.lbm_set_launch.argtypes = [H, C.c_int32, C.c_int32]
         L.lbm_measure_peaks.argtypes = [vp, d, d]
         B = C.c_void_p
         L.lbm_batch_create.argtypes = [C.c_size_t, C.c_int32, vp, P(B)]
@@ -351,6 +352,11 @@ class Lattice:
         k = lbm_kernel_info()
         _check(lib().lbm_tune(self._h, int(steps_per_trial), C.byref(k)), "lbm_tune")
         return {n: getattr(k, n) for n, _ in lbm_kernel_info._fields_}
+
+    def set_launch(self, row_block: int, ctas_per_sm: int = 2) -> dict:
+        """lbm_set_launch: fix the launch geometry; returns kernel_info."""
+        _check(lib().lbm_set_launch(self._h, int(row_block), int(ctas_per_sm)), "lbm_set_launch")
+        return self.kernel_info()
 
     def kernel_info(self) -> dict:
         """Launch geometry of the step kernel (lbm_get_kernel_info)."""

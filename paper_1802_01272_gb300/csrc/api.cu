@@ -612,6 +612,26 @@ int lbm_step(lbm_handle* h, int64_t n) {
   return LBM_OK;
 }
 
+int lbm_set_launch(lbm_handle* h, int32_t row_block, int32_t ctas_per_sm) {
+  if (!h || row_block < 1 || ctas_per_sm < 1) return LBM_ERR_INVALID_ARG;
+  const int lim = h->p.ctu_order == 1 ? 0 : h->p.limiter;
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+  const int occ = h->elem == 4   ? step_occupancy_f32(h->p.ctu_order, lim, h->vec, h->smem)
+                  : h->elem == 2 ? step_occupancy_f16(h->p.ctu_order, lim, h->vec, h->smem)
+                                 : step_occupancy_f64(h->p.ctu_order, lim, h->vec, h->smem);
+  if (nsm < 1 || occ < 1) return set_err(h, LBM_ERR_CUDA);
+  if (ctas_per_sm > occ) return LBM_ERR_INVALID_ARG;
+  const long long items = (long long)((h->p.Ly + row_block - 1) / row_block) * h->nstrip;
+  const long long gmax = (long long)nsm * ctas_per_sm;
+  h->row_block = row_block;
+  h->grid = (int)(items < gmax ? items : gmax);
+  h->a32.row_block = h->a64.row_block = row_block;
+  h->a32.items = h->a64.items = items;
+  drop_graphs(h);  // built for the old geometry
+  return LBM_OK;
+}
+
 int lbm_tune(lbm_handle* h, int32_t steps_per_trial, lbm_kernel_info* out) {
   if (!h || steps_per_trial < 1) return LBM_ERR_INVALID_ARG;
   const int lim = h->p.ctu_order == 1 ? 0 : h->p.limiter;

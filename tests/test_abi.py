@@ -114,3 +114,4 @@ def test_batch_server_argument_checks(P):
     L.lbm_batch_destroy(None)
     assert L.lbm_tune(None, 3, None) == -1
     assert L.lbm_measure_peaks(None, None, None) == -1
+    assert L.lbm_set_launch(None, 96, 2) == -1

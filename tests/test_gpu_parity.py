@@ -311,5 +311,7 @@ def test_tune_picks_a_geometry_and_keeps_results(P):
             assert n >= 2 * 4
             assert k == A.kernel_info() and 16 <= k["row_block"] <= 1024
             A.step(40)
+            B.set_launch(24, 1)          # any geometry: the same state
             B.step(n + 40)
+            assert B.kernel_info()["row_block"] == 24
             assert np.array_equal(A.get_f(), B.get_f())

@@ -15,6 +15,16 @@ so no flush is needed between steps.
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank advances its own independent lattice
 (replicas; the step has no exchange), timings are max-reduced.
+
+The JSON line adds to the common fields: `roofline` (HBM: algorithmic bytes
+per step / step time against MEASURED_PEAKS.json `hbm_gbs`, with the DRAM
+traffic of the committed ncu capture of this kernel source), `issue_roofline`
+and `fp32_roofline` (instructions and FP32 flops per node update from the
+committed capture, against the peaks the library measures on the device with
+lbm_measure_peaks), `e2e` (the same metric through the C ABI with pinned host
+buffers, copies inside the timed region), `cpu_baseline` (the FP64 oracle on
+the host cores and on one thread), `clocks`, and `config.launch` (the launch
+geometry lbm_tune chose before the warm-up, or --row-block's).
 """
 from __future__ import annotations
 

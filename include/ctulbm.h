@@ -124,11 +124,18 @@ int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out);
 /* Free every device allocation of the handle (synchronises its stream). NULL is a no-op. */
 void lbm_destroy(lbm_handle* h);
 
-/* f_k = f_k^eq(rho, u) (Eq. herfeq) at every node, from host FP64 fields [Ly][Lx]. */
+/* f_k = f_k^eq(rho, u) (Eq. herfeq) at every node, from FP64 fields [Ly][Lx]:
+ * host arrays (copied, then the stream is synchronised), or device arrays
+ * for the _device variant (asynchronous; the caller keeps them alive until
+ * the stream reaches this call).  The caller owns the arrays.  Resets the
+ * step count. */
 int lbm_init_rho_u(lbm_handle* h, const double* rho, const double* ux, const double* uy);
 int lbm_init_rho_u_device(lbm_handle* h, const double* rho, const double* ux, const double* uy);
 
-/* Copy distributions in or out, FP64 [16][Ly][Lx] (converted to/from the storage precision). */
+/* Copy distributions in or out, FP64 [16][Ly][Lx] in velocity order
+ * (converted to/from the storage precision and layout); host variants
+ * synchronise the stream, _device variants take device pointers and are
+ * asynchronous.  lbm_set_f* resets the step count. */
 int lbm_set_f(lbm_handle* h, const double* f);
 int lbm_get_f(lbm_handle* h, double* f);
 int lbm_set_f_device(lbm_handle* h, const double* f);
@@ -154,7 +161,8 @@ int lbm_step_diag(lbm_handle* h, int64_t n, double threshold, lbm_diag* out);
  * on their own.  Every node goes through the same sequence of operations as in
  * lbm_step; the batched kernel is compiled separately, so FP32 results agree
  * with stepping alone to rounding (the compiler may fuse multiply-adds
- * differently), FP64 lattices step alone and agree exactly.  All handles must share
+ * differently), FP64 lattices step alone and agree exactly; a lattice alone in
+ * its group takes lbm_step's path (graph launches).  All handles must share
  * one device and one stream (handles[0]'s); asynchronous like lbm_step.
  * Returns LBM_ERR_INVALID_ARG for a null or repeated handle or a stream
  * mismatch. */

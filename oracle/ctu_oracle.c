@@ -12,9 +12,11 @@
  *   - force term F_k ...................... Eq. (herforce), a^(2) read as the
  *                                           equilibrium a^(2) = rho(uu + (T-1)1)
  *   - acceleration g ...................... Eq. (eder) with the vdW pressure of
- *                                           Eq. (evdw); 25-point footprint from an
- *                                           isotropic 3x3 gradient and 9-point
- *                                           Laplacian (the paper gives no weights)
+ *                                           Eq. (evdw); 25-point (5x5) stencils:
+ *                                           a fourth-order gradient of p^i - p^w,
+ *                                           and grad(lap rho) from an isotropic
+ *                                           3x3 gradient of the 9-point Laplacian
+ *                                           (the paper gives no weights)
  *   - CTU1 ................................ Eq. (ctueq), four-node product form
  *   - CTU2 ................................ Sec. II C 2: jumps R, limited
  *                                           corrections S (MC limiter), fluxes F, G
@@ -37,8 +39,9 @@
  * collision.
  *
  * Parity of the force stencil and of a^(2) against the paper itself is
- * pinned only indirectly (convergence, isotropy, Maxwell coexistence), since
- * the paper prints neither the stencil weights nor the label of a^(2).
+ * pinned only indirectly (convergence order, isotropy, and on the GPU the
+ * coexistence densities and critical radius the paper reports), since the
+ * paper prints neither the stencil weights nor the label of a^(2).
  */
 #include "ctu_oracle.h"
 
@@ -204,12 +207,26 @@ void orc_init_feq(const orc_params* p, const double* rho, const double* ux, cons
 }
 
 /* ---- Eq. (eder): g = grad(p^i - p^w)/rho + kappa grad(lap rho) -----------
- * Isotropic 3x3 gradient:
+ * Sec. II B computes both terms on 25-point stencils, chosen there because
+ * large stencils make the interface more isotropic and the coexistence
+ * densities more accurate.  The weights are not printed; the ones used here:
+ *
+ * Isotropic 3x3 gradient D_h (error (ds^2/6) grad lap q, the same in every
+ * direction):
  *   d_x q = [ (q(i+1,j) - q(i-1,j))/3
  *           + (q(i+1,j+1) - q(i-1,j+1) + q(i+1,j-1) - q(i-1,j-1))/12 ] / ds
+ * Fourth-order gradient on the 5x5 square, the Richardson combination
+ * (4 D_h - D_2h)/3 of D_h at spacings ds and 2 ds, which cancels that error:
+ *   d_x q = [ 4/9 (q(i+1,j) - q(i-1,j))
+ *           + 1/9 (q(i+1,j+1) - q(i-1,j+1) + q(i+1,j-1) - q(i-1,j-1))
+ *           - 1/18 (q(i+2,j) - q(i-2,j))
+ *           - 1/72 (q(i+2,j+2) - q(i-2,j+2) + q(i+2,j-2) - q(i-2,j-2)) ] / ds
+ *   (on a planar profile it is the five-point fourth-order difference
+ *    [8 (q(+1) - q(-1)) - (q(+2) - q(-2))] / 12)
  * Isotropic 9-point Laplacian:
  *   lap q = [ 2/3 (4 nearest) + 1/6 (4 diagonal) - 10/3 q(i,j) ] / ds^2
- * grad(lap rho) composes them: a 5x5 = 25-point footprint.                 */
+ * grad(p^i - p^w) takes the fourth-order gradient; grad(lap rho) the 3x3
+ * gradient of the Laplacian, which composes to the 5x5 square as well.    */
 typedef struct {
   int Lx, nrow, j0; /* rows j0 .. j0+nrow-1 */
   double* v;
@@ -228,6 +245,23 @@ static void grad_iso(const rowfield* q, int i, int j, double ds, double* gx, dou
              12.0) / ds;
 }
 
+static void grad_4th(const rowfield* q, int i, int j, double ds, double* gx, double* gy) {
+  *gx = (4.0 / 9.0 * (rf(q, i + 1, j) - rf(q, i - 1, j)) +
+         1.0 / 9.0 *
+             (rf(q, i + 1, j + 1) - rf(q, i - 1, j + 1) + rf(q, i + 1, j - 1) - rf(q, i - 1, j - 1)) -
+         1.0 / 18.0 * (rf(q, i + 2, j) - rf(q, i - 2, j)) -
+         1.0 / 72.0 *
+             (rf(q, i + 2, j + 2) - rf(q, i - 2, j + 2) + rf(q, i + 2, j - 2) - rf(q, i - 2, j - 2))) /
+        ds;
+  *gy = (4.0 / 9.0 * (rf(q, i, j + 1) - rf(q, i, j - 1)) +
+         1.0 / 9.0 *
+             (rf(q, i + 1, j + 1) - rf(q, i + 1, j - 1) + rf(q, i - 1, j + 1) - rf(q, i - 1, j - 1)) -
+         1.0 / 18.0 * (rf(q, i, j + 2) - rf(q, i, j - 2)) -
+         1.0 / 72.0 *
+             (rf(q, i + 2, j + 2) - rf(q, i + 2, j - 2) + rf(q, i - 2, j + 2) - rf(q, i - 2, j - 2))) /
+        ds;
+}
+
 static double lap_iso(const rowfield* q, int i, int j, double ds) {
   double nn = rf(q, i + 1, j) + rf(q, i - 1, j) + rf(q, i, j + 1) + rf(q, i, j - 1);
   double dg = rf(q, i + 1, j + 1) + rf(q, i - 1, j + 1) + rf(q, i + 1, j - 1) + rf(q, i - 1, j - 1);
@@ -239,23 +273,23 @@ static void accel_field(const lattice* L, double* gx, double* gy) {
   const orc_params* p = L->p;
   const int Lx = p->Lx, Ly = p->Ly;
   rowfield rho = {Lx, Ly + 4, -2, malloc(sizeof(double) * Lx * (Ly + 4))};
-  rowfield phi = {Lx, Ly + 2, -1, malloc(sizeof(double) * Lx * (Ly + 2))};
+  rowfield phi = {Lx, Ly + 4, -2, malloc(sizeof(double) * Lx * (Ly + 4))};
   rowfield lap = {Lx, Ly + 2, -1, malloc(sizeof(double) * Lx * (Ly + 2))};
 #pragma omp parallel for schedule(static) if (PAR(p))
   for (int j = -2; j < Ly + 2; ++j)
     for (int i = 0; i < Lx; ++i) rho.v[(size_t)(j + 2) * Lx + i] = rho_at(L, i, j);
 #pragma omp parallel for schedule(static) if (PAR(p))
-  for (int j = -1; j < Ly + 1; ++j)
+  for (int j = -2; j < Ly + 2; ++j)
     for (int i = 0; i < Lx; ++i) {
       double r = rf(&rho, i, j);
-      phi.v[(size_t)(j + 1) * Lx + i] = r * p->T - orc_pw(p, r); /* p^i - p^w */
-      lap.v[(size_t)(j + 1) * Lx + i] = lap_iso(&rho, i, j, p->ds);
+      phi.v[(size_t)(j + 2) * Lx + i] = r * p->T - orc_pw(p, r); /* p^i - p^w */
+      if (j >= -1 && j < Ly + 1) lap.v[(size_t)(j + 1) * Lx + i] = lap_iso(&rho, i, j, p->ds);
     }
 #pragma omp parallel for schedule(static) if (PAR(p))
   for (int j = 0; j < Ly; ++j)
     for (int i = 0; i < Lx; ++i) {
       double px, py, lx, ly;
-      grad_iso(&phi, i, j, p->ds, &px, &py);
+      grad_4th(&phi, i, j, p->ds, &px, &py);
       grad_iso(&lap, i, j, p->ds, &lx, &ly);
       double r = rf(&rho, i, j);
       gx[(size_t)j * Lx + i] = px / r + p->kappa * lx;

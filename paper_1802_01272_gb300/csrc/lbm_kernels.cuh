@@ -4,7 +4,8 @@
 // One step, as Sec. II C splits Eq. (eBGK): advection of each f_k over its
 // upwind-corner stencil (CTU1, Eq. ctueq; CTU2 with the MC limiter,
 // Sec. II C 2), then on the advected f*: rho, u, g (Eq. eder with Eq. evdw,
-// isotropic 25-point stencil), f^eq (Eq. herfeq), F_k (Eq. herforce), BGK
+// 25-point stencils: fourth-order gradient of p^i - p^w, isotropic gradient of
+// the 9-point Laplacian), f^eq (Eq. herfeq), F_k (Eq. herforce), BGK
 // relaxation (optionally regularised, Eq. ereg), and the density reservoir of
 // Sec. III A.
 //
@@ -25,8 +26,9 @@
 //       live in registers) into a ring of advected rows f*;
 //   P2  one thread per node: rho*, u*, p^i - p^w of rows a0..a0+3;
 //   P3  one thread per node: 9-point Laplacian of rho* on rows a0-1..a0+2;
-//   P4  one thread per node on rows a0-2..a0+1: isotropic gradients -> g, the
-//       collision coefficients, then all 16 planes relaxed and stored
+//   P4  one thread per node on rows a0-2..a0+1: gradients (5x5 of p^i - p^w,
+//       3x3 of the Laplacian) -> g, the collision coefficients, then all 16
+//       planes relaxed and stored
 //       (coalesced 128-byte warp stores per plane).
 // Four CTA barriers per four rows.  Global memory is read once per step for
 // f^n (halo columns of neighbouring strips are L2 hits) and written once.

@@ -424,13 +424,22 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
           const int sc = (c & (MROWS - 1)) * REG + col;
           const int sm = ((c - 1) & (MROWS - 1)) * REG + col;
           const int sp = ((c + 1) & (MROWS - 1)) * REG + col;
+          const int s2m = ((c - 2) & (MROWS - 1)) * REG + col;
+          const int s2p = ((c + 2) & (MROWS - 1)) * REG + col;
           const T* ph = S.phi;
           const T* lp = S.lap;
-          // isotropic gradient: [ (q(+1,0)-q(-1,0))/3 + (diagonal differences)/12 ] / ds
-          const T px = (ph[sc + 1] - ph[sc - 1]) * T(1.0 / 3.0) +
-                       (ph[sp + 1] - ph[sp - 1] + ph[sm + 1] - ph[sm - 1]) * T(1.0 / 12.0);
-          const T py = (ph[sp] - ph[sm]) * T(1.0 / 3.0) +
-                       (ph[sp + 1] - ph[sm + 1] + ph[sp - 1] - ph[sm - 1]) * T(1.0 / 12.0);
+          // fourth-order 5x5 gradient of p^i - p^w: the combination (4 D_h - D_2h)/3
+          // of the isotropic 3x3 gradient D_h at spacings ds and 2 ds
+          const T px = (ph[sc + 1] - ph[sc - 1]) * T(4.0 / 9.0) +
+                       (ph[sp + 1] - ph[sp - 1] + ph[sm + 1] - ph[sm - 1]) * T(1.0 / 9.0) -
+                       (ph[sc + 2] - ph[sc - 2]) * T(1.0 / 18.0) -
+                       (ph[s2p + 2] - ph[s2p - 2] + ph[s2m + 2] - ph[s2m - 2]) * T(1.0 / 72.0);
+          const T py = (ph[sp] - ph[sm]) * T(4.0 / 9.0) +
+                       (ph[sp + 1] - ph[sm + 1] + ph[sp - 1] - ph[sm - 1]) * T(1.0 / 9.0) -
+                       (ph[s2p] - ph[s2m]) * T(1.0 / 18.0) -
+                       (ph[s2p + 2] - ph[s2m + 2] + ph[s2p - 2] - ph[s2m - 2]) * T(1.0 / 72.0);
+          // isotropic 3x3 gradient of the Laplacian:
+          // [ (q(+1,0)-q(-1,0))/3 + (diagonal differences)/12 ] / ds
           const T lx = (lp[sc + 1] - lp[sc - 1]) * T(1.0 / 3.0) +
                        (lp[sp + 1] - lp[sp - 1] + lp[sm + 1] - lp[sm - 1]) * T(1.0 / 12.0);
           const T ly = (lp[sp] - lp[sm]) * T(1.0 / 3.0) +

@@ -16,50 +16,75 @@ GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_v
 
 def test_planar_interface_surface_tension():
     """Sec. III A: sigma of the relaxed planar interface at T = 0.8, kappa = 1e-4,
-    ds = 1/256, tau = 1e-3 (the paper: 4.8747e-3; ours is 1 % lower, within the
-    spread of numerical derivatives over an 11-node interface).  The liquid
-    plateau sits on the Maxwell density; the vapour plateau 3.4 % below it (the
-    paper reports LB densities that approach the Maxwell values as tau -> 0,
-    Sec. II E)."""
+    ds = 1/256, tau = 1e-3 (the paper: 4.8747e-3; measured +0.07 %), with the
+    liquid plateau on the Maxwell density and the vapour plateau 1 % below it.
+    FP32 shifted storage (its coexistence matches FP64 to 1e-6)."""
+    import paper_1802_01272_gb300 as P
     from paper_1802_01272_gb300 import eos
     from paper_1802_01272_gb300 import experiments as X
-    sigma, prof = X.planar_interface_sigma()
+    sigma, prof = X.planar_interface_sigma(precision=P.LBM_FP32_SHIFTED)
     want = GOLD["surface_tension_T0.8_kappa1e-4"]["ds_1_256"]
     rl, rv = eos.coexistence(0.8)
     print(f"\nsigma planar = {sigma:.6e} paper {want:.6e} rel {(sigma - want) / want:+.2e}; "
           f"rho_L {prof.max():.6f} ({rl:.6f}) rho_V {prof.min():.6f} ({rv:.6f})")
-    assert abs(sigma - want) / want < 2e-2
-    assert abs(prof.max() - rl) / rl < 1e-3 and abs(prof.min() - rv) / rv < 5e-2
+    assert abs(sigma - want) / want < 5e-3
+    assert abs(prof.max() - rl) / rl < 1e-3 and abs(prof.min() - rv) / rv < 2e-2
+
+
+def test_phase_diagram_vapour_density_against_maxwell():
+    """Sec. II E: planar-interface coexistence densities on the paper's grid
+    (CTU2, tau = 1e-3, dt = 1e-4, ds = 1/256) stay close to Maxwell's from
+    T = 0.7 up, while at T = 0.6 the vapour density sits about 8 % under it
+    (measured: -3.2 % at T = 0.7, -1.0 % at 0.8, -10.2 % at 0.6)."""
+    import paper_1802_01272_gb300 as P
+    from paper_1802_01272_gb300 import eos
+    from paper_1802_01272_gb300 import experiments as X
+    g = GOLD["phase_diagram_vapour_deviation"]
+    dev = {}
+    for T in (g["T_low"], g["T_good_agreement_min"], 0.8):
+        _, prof = X.planar_interface_sigma(T=T, Lx=128, t_end=20.0, precision=P.LBM_FP32_SHIFTED)
+        rl, rv = eos.coexistence(T)
+        dev[T] = (prof.max() / rl - 1.0, prof.min() / rv - 1.0)
+        print(f"\nT={T}: rho_L {dev[T][0]:+.3e} rho_V {dev[T][1]:+.3e} of Maxwell")
+    for T in (g["T_good_agreement_min"], 0.8):
+        assert abs(dev[T][0]) < 2e-3 and abs(dev[T][1]) < 0.05
+    low = -dev[g["T_low"]][1]
+    assert abs(low - g["vapour_rel_diff_at_T_low"]) < 0.04 and abs(dev[g["T_low"]][0]) < 2e-3
+    assert low > -dev[g["T_good_agreement_min"]][1] > -dev[0.8][1] > 0
 
 
 def test_coexistence_approaches_maxwell_as_tau_decreases():
     """Sec. II E (dependence of rho_L, rho_V on tau at T = 0.8): the planar
     interface's vapour density moves toward the Maxwell value as tau falls."""
+    import paper_1802_01272_gb300 as P
     from paper_1802_01272_gb300 import eos
     from paper_1802_01272_gb300 import experiments as X
     _, rv = eos.coexistence(0.8)
     dev = []
     for tau in (1e-2, 1e-3):
-        _, prof = X.planar_interface_sigma(tau=tau, t_end=30.0)
+        _, prof = X.planar_interface_sigma(tau=tau, t_end=30.0, precision=P.LBM_FP32_SHIFTED)
         dev.append(abs(prof.min() - rv) / rv)
         print(f"\ntau={tau}: rho_V {prof.min():.6f} (Maxwell {rv:.6f}) rel {dev[-1]:.3e}")
     assert dev[1] < dev[0]
 
 
-def test_critical_radius_brackets_growth_and_collapse():
-    """Sec. III A: with the liquid held at rho_ext = 1.923 (T = 0.8), a bubble
-    below Eq. (raggio_c)'s radius (75.7 ds) collapses and one above it grows."""
+def test_critical_radius_matches_the_paper():
+    """Sec. III A: with the liquid held at rho_ext = 1.923 (T = 0.8, L = 1024,
+    ds = 1/256), the paper's lattice gives R_c = 76.5 ds (Eq. raggio_c: 75.7).
+    A bubble seeded 1.5 nodes under it collapses and one 1.5 nodes over it
+    grows."""
     from paper_1802_01272_gb300 import eos
     from paper_1802_01272_gb300 import experiments as X
-    rc = X.critical_radius(0.8, 1.923, eos.interface_tension(0.8, 1e-4)) * 256
-    print(f"\nR_c pred = {rc:.2f} nodes")
-    small = X.bubble_in_reservoir(rc - 15, 1.923, t_end=4.0, every=0.25)
-    large = X.bubble_in_reservoir(rc + 25, 1.923, t_end=4.0, every=0.25)
+    rc = GOLD["critical_radius_rho_ext_1.923"]["Rc_over_ds"]
+    pred = X.critical_radius(0.8, 1.923, eos.interface_tension(0.8, 1e-4)) * 256
+    print(f"\nR_c paper lattice {rc} nodes, Eq. raggio_c {pred:.2f} nodes")
+    small = X.bubble_in_reservoir(rc - 1.5, 1.923, t_end=8.0, every=0.5)
+    large = X.bubble_in_reservoir(rc + 1.5, 1.923, t_end=8.0, every=0.5)
     print("small R(t) nodes", np.round(small.R * 256, 2))
     print("large R(t) nodes", np.round(large.R * 256, 2))
     i = int(np.searchsorted(small.t, 1.0))
-    assert small.R[-1] * 256 < small.R[i] * 256 - 2.0
-    assert large.R[-1] * 256 > large.R[i] * 256 + 1.0
+    assert small.R[-1] * 256 < small.R[i] * 256 - 3.0
+    assert large.R[-1] * 256 > large.R[i] * 256 + 1.5
 
 
 def test_rayleigh_plesset_growth():

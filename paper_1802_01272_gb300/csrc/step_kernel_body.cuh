@@ -87,8 +87,7 @@ struct Smem {
   T* phi;     // p^i - p^w
   T* lap;     // 9-point Laplacian of rho*
   int* col;   // [SG] wrapped global column of each staging group
-  double* dmass;              // fused diagnostics: per-CTA accumulators
-  unsigned long long* dsums;  // [6]
+  unsigned long long* dsums;  // [6] fused diagnostics: per-CTA bubble-site sums
   unsigned long long* bar;    // [2] mbarriers of the tensor-copy batches (even, odd)
   int* abort;                 // a bounded wait of this CTA timed out: stop waiting
   __device__ Smem(unsigned char* raw) {
@@ -105,8 +104,7 @@ struct Smem {
     phi = uy + MROWS * REG;
     lap = phi + MROWS * REG;
     col = reinterpret_cast<int*>(lap + MROWS * REG);
-    dmass = reinterpret_cast<double*>(col + SG + (SG & 1));  // 8-byte aligned after 18 ints
-    dsums = reinterpret_cast<unsigned long long*>(dmass + 1);
+    dsums = reinterpret_cast<unsigned long long*>(col + SG + (SG & 1));  // 8-byte aligned
     bar = dsums + 6;
     abort = reinterpret_cast<int*>(bar + 2);
   }
@@ -290,10 +288,10 @@ __device__ __forceinline__ void advect_rows(const StepArgs<T>& P, const Smem<T, 
 // One row segment [ys, ye) of one strip of one lattice.  Every node's update
 // uses the same arithmetic in the same order whatever the segment boundaries,
 // so results do not depend on how the rows are split over CTAs or lattices.
-template <typename T, typename ST, int ORDER, int LIM, bool VEC>
+template <typename T, typename ST, int ORDER, int LIM, bool VEC, bool DIAG>
 __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, ST>& S, int strip,
                                             int ys, int ye, const CUtensorMap* tm,
-                                            unsigned& batch) {
+                                            unsigned& batch, double& dmass) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   // P1 layout: a warp = one sign quadrant x two velocity groups x 16 column
@@ -341,6 +339,11 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
       stage_rows<T, ST, VEC>(P, S, slots, a0 + 1, a0 + RPI + 2, rbase);
     cp_async_commit();
 
+    // fused diagnostics: this thread's mass over the segment, as the sum of
+    // rho - rho_ref (small in the liquid, so FP32 keeps it exact to ~1e-7 of
+    // the node count) plus rho_ref times its node count
+    T dseg = T(0);
+    int nseg = 0;
     for (; a0 - 2 < ye; a0 += RPI) {
       // ---------------- L: prefetch the rows only the next iteration needs
       const bool more = (a0 + RPI) - 2 < ye;
@@ -549,15 +552,13 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
             }
           }
         }
-        if (P.diag_mass) {  // fused diagnostics: warp sums, then per-CTA shared accumulators
+        if (DIAG) {  // fused diagnostics: mass per thread, bubble sites per warp
           const bool on = rho_post >= T(0);
           const bool in = on && rho_post < P.diag_thr;
-          // warp sum in the storage precision (GB300's FP64 issue rate is
-          // low), accumulated per CTA in FP64
-          T m = on ? rho_post : T(0);
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) m += __shfl_down_sync(0xffffffffu, m, o);
-          if (lane == 0) atomicAdd(S.dmass, (double)m);
+          if (on) {
+            dseg += rho_post - P.rho_ref;
+            ++nseg;
+          }
           if (__ballot_sync(0xffffffffu, in)) {  // bubble sites are rare: sum them only here
             const unsigned long long i = in ? (unsigned long long)p4_x : 0ULL;
             const unsigned long long j = in ? (unsigned long long)c : 0ULL;
@@ -576,6 +577,7 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
       }
     }
     cp_async_wait<0>();
+    if (DIAG) dmass += (double)dseg + (double)P.rho_ref * (double)nseg;
   }
 }
 
@@ -600,14 +602,16 @@ __device__ __forceinline__ void retire_cta(unsigned long long* sched) {
   }
 }
 
-template <typename T, typename ST, int ORDER, int LIM, bool VEC>
+// DIAG: fuse the diagnostics of the state after the step (P.diag_mass and
+// P.diag_sums receive them); a separate instantiation so that the plain step
+// executes none of their instructions.
+template <typename T, typename ST, int ORDER, int LIM, bool VEC, bool DIAG>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     step_kernel(const __grid_constant__ StepArgs<T> P, const __grid_constant__ RowMaps maps) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const Smem<T, ST> S(smem_raw);
   __shared__ long long s_item;
   if (threadIdx.x == 0) {
-    *S.dmass = 0.0;
     for (int t = 0; t < 6; ++t) S.dsums[t] = 0ULL;
     *S.abort = 0;
     mbar_init(S.bar, 1);
@@ -616,6 +620,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
   }
   const CUtensorMap* tm = P.tma_ok ? maps.m : nullptr;
   unsigned batch = 0;  // tensor-copy batches issued (and consumed) by this CTA
+  double dmass = 0.0;  // fused diagnostics: this thread's mass over all its segments
   for (;;) {
     const long long item = claim_item(P.sched, &s_item);
     if (item >= P.items) break;
@@ -623,12 +628,16 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     const int strip = (int)(item - rb * P.nstrip);
     const int ys = (int)(rb * P.row_block);
     const int ye = min(P.Ly, ys + P.row_block);
-    run_segment<T, ST, ORDER, LIM, VEC>(P, S, strip, ys, ye, tm, batch);
+    run_segment<T, ST, ORDER, LIM, VEC, DIAG>(P, S, strip, ys, ye, tm, batch, dmass);
   }
-  // claim_item's barrier after the last claim orders every warp's shared adds
-  if (P.diag_mass && threadIdx.x == 0) {
-    atomicAdd(P.diag_mass, *S.dmass);
-    for (int t = 0; t < 6; ++t) atomicAdd(&P.diag_sums[t], S.dsums[t]);
+  if (DIAG) {
+    // one warp sum and one global add per warp for the mass; claim_item's
+    // barrier after the last claim orders every warp's shared site sums
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmass += __shfl_down_sync(0xffffffffu, dmass, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(P.diag_mass, dmass);
+    if (threadIdx.x == 0)
+      for (int t = 0; t < 6; ++t) atomicAdd(&P.diag_sums[t], S.dsums[t]);
   }
   retire_cta(P.sched);
 }
@@ -643,6 +652,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
   __shared__ long long s_item;
   int i = 0;
   unsigned batch = 0;  // unused: batched lattices stage by per-thread copies
+  double dmass = 0.0;  // unused: batched launches carry no fused diagnostics
   for (;;) {
     const long long item = claim_item(B.sched, &s_item);
     if (item >= B.item_start[B.count]) break;
@@ -653,7 +663,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     const int strip = (int)(local - rb * P.nstrip);
     const int ys = (int)(rb * P.row_block);
     const int ye = min(P.Ly, ys + P.row_block);
-    run_segment<T, T, ORDER, LIM, VEC>(P, S, strip, ys, ye, nullptr, batch);
+    run_segment<T, T, ORDER, LIM, VEC, false>(P, S, strip, ys, ye, nullptr, batch, dmass);
   }
   retire_cta(B.sched);
 }

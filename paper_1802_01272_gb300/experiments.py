@@ -112,14 +112,15 @@ class BubbleRun:
 
 def bubble_in_reservoir(R0_nodes, rho_ext, T=0.8, kappa=1e-4, ds=1 / 256, L=1024, tau=1e-3,
                         t_end=4.0, every=0.1, rho_v=None, precision=LBM_FP32_SHIFTED,
-                        stream=None) -> BubbleRun:
+                        stream=None, width=1.0) -> BubbleRun:
     """Sec. III A-B: a vapour bubble (rho_v, default the coexistence vapour)
     in a superheated liquid held at rho_ext outside R_BC = [L/2 - 1/(2 ds)] ds
-    by the reservoir rescale.  Records R(t) from the bubble-site count
+    by the reservoir rescale, seeded as a tanh profile of `width` nodes (a
+    step as width -> 0).  Records R(t) from the bubble-site count
     (rho < (rho_V + rho_L)/2), rho at the centre and on the ring r = R_BC."""
     rl, rv = eos.coexistence(T)
     rho_v = rv if rho_v is None else rho_v
-    rho, ux, uy = bubble_fields(L, L, R0_nodes, rho_v, rho_ext, 1.0)
+    rho, ux, uy = bubble_fields(L, L, R0_nodes, rho_v, rho_ext, width)
     p = _params(L, L, T, tau, kappa, ds, precision, rho_ext, reservoir=1, rho_ext=rho_ext)
     thr = 0.5 * (rl + rv)
     r_inf_nodes = L / 2 - 1.0 / (2.0 * ds)

@@ -92,7 +92,8 @@ def test_rayleigh_plesset_growth():
     predicts from the pressures measured at its centre and at r_inf = R_BC,
     starting from the lattice state after the interface has relaxed (t = 2);
     2048^2 nodes, so that r_inf / R stays large (the paper notes RP holds only
-    while that ratio is large)."""
+    while that ratio is large).  Measured: RP ends 2 % of the growth away
+    from the lattice radius."""
     from paper_1802_01272_gb300 import experiments as X
     run = X.bubble_in_reservoir(110, 1.923, L=2048, t_end=8.0, every=0.1)
     t, R = X.rp_prediction(run, 2.0)
@@ -102,7 +103,7 @@ def test_rayleigh_plesset_growth():
     print("R_RP nodes", np.round(R[::10] * 256, 2))
     growth = lb[-1] - lb[0]
     assert growth * 256 > 3.0
-    assert abs(R[-1] - lb[-1]) < 0.25 * growth
+    assert abs(R[-1] - lb[-1]) < 0.1 * growth
 
 
 def test_sheared_bubble_deformation_and_tilt():

@@ -335,6 +335,50 @@ def test_force_stencil_orders_and_isotropic(oracle_mod):
         assert lo < errs[0] / errs[1] < hi
 
 
+def test_force_stencils_exact_on_polynomials(oracle_mod):
+    """The force stencils of Eq. (eder) are exact on low-degree polynomials
+    away from the periodic seam: the fourth-order 5x5 gradient of p^i - p^w
+    differentiates quartics exactly (a second-order 3x3 gradient would not),
+    and the 3x3 gradient of the 9-point Laplacian gives grad(lap rho) exactly
+    for cubics.  b = 0 makes p^i - p^w = a rho^2, so rho = sqrt(P4) puts a
+    quartic under the pressure gradient; a = b = 0 leaves the kappa term alone."""
+    O = oracle_mod
+    n = 20
+    ds = 1.0 / n
+    j, i = np.mgrid[0:n, 0:n].astype(np.float64)
+    x, y = i * ds, j * ds
+    inner = (slice(2, n - 2), slice(2, n - 2))   # stencils that do not cross the seam
+    zero = np.zeros((n, n))
+    # pressure term: p^i - p^w = a rho^2 = a P4
+    P4 = (2 + 0.3 * x - 0.2 * y + 0.5 * x * x + 0.4 * x * y - 0.3 * y * y + 0.7 * x ** 3
+          - 0.2 * x * x * y + 0.6 * x * y * y - 0.4 * y ** 3 + 0.9 * x ** 4 + 0.3 * x ** 3 * y
+          - 0.5 * x * x * y * y + 0.2 * x * y ** 3 + 0.4 * y ** 4)
+    dP4x = (0.3 + 1.0 * x + 0.4 * y + 2.1 * x * x - 0.4 * x * y + 0.6 * y * y + 3.6 * x ** 3
+            + 0.9 * x * x * y - 1.0 * x * y * y + 0.2 * y ** 3)
+    dP4y = (-0.2 + 0.4 * x - 0.6 * y - 0.2 * x * x + 1.2 * x * y - 1.2 * y * y + 0.3 * x ** 3
+            - 1.0 * x * x * y + 0.6 * x * y * y + 1.6 * y ** 3)
+    assert P4.min() > 1.0
+    a = 9 / 8
+    p = params(O, Lx=n, Ly=n, ds=ds, T=0.9, kappa=0.0, a=a, b=0.0)
+    rho = np.sqrt(P4)
+    gx, gy = O.accel(p, O.init_feq(p, rho, zero, zero))
+    ex, ey = a * dP4x / rho, a * dP4y / rho
+    err = max(np.abs(gx - ex)[inner].max(), np.abs(gy - ey)[inner].max())
+    print(f"\npressure term on a quartic: max error {err:.2e} (|g| ~ {np.abs(ex).max():.2f})")
+    assert err < 1e-9
+    # kappa term: grad(lap P3) is constant
+    P3 = 1.5 + 0.2 * x + 0.1 * y + 0.3 * x * x - 0.2 * x * y + 0.25 * y * y + 0.4 * x ** 3 \
+        - 0.3 * x * x * y + 0.5 * x * y * y - 0.2 * y ** 3
+    kappa = 1e-3
+    p = params(O, Lx=n, Ly=n, ds=ds, T=0.9, kappa=kappa, a=0.0, b=0.0)
+    gx, gy = O.accel(p, O.init_feq(p, P3, zero, zero))
+    want_x = kappa * (6 * 0.4 + 2 * 0.5)        # d/dx of lap P3 = 6 c30 + 2 c12
+    want_y = kappa * (2 * (-0.3) + 6 * (-0.2))  # d/dy of lap P3 = 2 c21 + 6 c03
+    err = max(np.abs(gx - want_x)[inner].max(), np.abs(gy - want_y)[inner].max())
+    print(f"kappa term on a cubic: max error {err:.2e} (|g| ~ {abs(want_x):.2e})")
+    assert err < 1e-9
+
+
 # ------------------------------------------------------ boundaries (Sec. III)
 def test_reservoir_sets_outside_density(oracle_mod):
     O = oracle_mod

@@ -10,7 +10,9 @@
  *      (Eq. ctueq) or CTU2 (jumps R, MC-limited corrections S, fluxes F, G of
  *      Sec. II C 2);
  *   2. on the advected f: rho, u (Sec. II A), the van der Waals acceleration
- *      g (Eq. eder, vdW pressure Eq. evdw, isotropic 25-point stencil),
+ *      g (Eq. eder, vdW pressure Eq. evdw; the 25-point stencils of Sec. II B:
+ *      a fourth-order 5x5 gradient of p^i - p^w and the isotropic 3x3
+ *      gradient of the 9-point Laplacian of rho),
  *      f^eq (Eq. herfeq), F_k (Eq. herforce) and the BGK relaxation
  *      f <- f - dt/tau (f - f^eq) + dt F_k, optionally regularised (Eq. ereg);
  *   3. optionally the density reservoir of Sec. III A (rescale f outside R_BC).

@@ -418,6 +418,11 @@ int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out) {
   x.Tt = p->T;
   std::memcpy(x.xi, h->xi, sizeof(h->xi));
   std::memcpy(x.w, h->w, sizeof(h->w));
+  for (int k = 0; k < 16; ++k) {
+    x.xif[k][0] = (float)h->xi[k][0];
+    x.xif[k][1] = (float)h->xi[k][1];
+    x.wf[k] = (float)h->w[k];
+  }
   *out = h;
   return LBM_OK;
 }

@@ -22,16 +22,30 @@ struct Comp<double> {
   using type = double;
 };
 
-// Velocity table in the storage precision, loaded once per thread.
+// Velocity table in the arithmetic precision, loaded once per thread.  The
+// float table comes rounded from the host, so the one-node-per-thread kernels
+// do no double -> float conversions (GB300's FP64 path is narrow).
 template <typename T>
 struct Vel {
   T x[16], y[16], w[16];
   __device__ explicit Vel(const AuxArgs& a) {
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      x[k] = (T)a.xi[k][0];
-      y[k] = (T)a.xi[k][1];
-      w[k] = (T)a.w[k];
+      x[k] = a.xi[k][0];
+      y[k] = a.xi[k][1];
+      w[k] = a.w[k];
+    }
+  }
+};
+template <>
+struct Vel<float> {
+  float x[16], y[16], w[16];
+  __device__ explicit Vel(const AuxArgs& a) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      x[k] = a.xif[k][0];
+      y[k] = a.xif[k][1];
+      w[k] = a.wf[k];
     }
   }
 };

@@ -19,6 +19,7 @@ struct AuxArgs {
   int storage;       // STORE_F32 / STORE_F16: f - w_k rho_ref as float / half; STORE_F64: f
   double rho_ref, Tt;
   double xi[16][2], w[16];
+  float xif[16][2], wf[16];  // the same tables rounded to float on the host
 };
 
 // One fused step kernel: returns cudaSuccess or the launch error.

@@ -3,7 +3,8 @@
 * surface tension of a relaxed planar interface, sigma = kappa int (d rho/dx)^2 dx
   (Eq. sigma, in the reading whose values the paper prints);
 * the critical radius of Eq. (raggio_c) and the growth or collapse of bubbles
-  around it with the density reservoir of Sec. III A;
+  around it with the density reservoir of Sec. III A, and the lattice's own
+  critical radius by bisection on the seed radius as Sec. III A estimates it;
 * bubble growth against the two-dimensional Rayleigh-Plesset equation
   (Eq. rp), fed with the pressures measured on the lattice as in Sec. III B;
 * a bubble deformed by the shear between moving walls (Sec. III C): shape
@@ -139,6 +140,48 @@ def bubble_in_reservoir(R0_nodes, rho_ext, T=0.8, kappa=1e-4, ds=1 / 256, L=1024
             ri.append(d["rho_ring"])
     return BubbleRun(t=np.array(t), R=np.array(R), rho_center=np.array(rc), rho_inf=np.array(ri),
                      r_inf=r_inf_nodes * ds, params=p)
+
+
+def bubble_fate(run: BubbleRun, t_relax=1.0, margin_nodes=1.0) -> int:
+    """+1 if the bubble of a reservoir run grew by more than `margin_nodes`
+    after the seed's interface relaxed (t >= t_relax), -1 if it shrank by
+    more, 0 if undecided over the run."""
+    ds = run.params.ds
+    i = int(np.searchsorted(run.t, t_relax - 1e-12))
+    change = (run.R[-1] - run.R[min(i, len(run.R) - 1)]) / ds
+    return 1 if change > margin_nodes else (-1 if change < -margin_nodes else 0)
+
+
+def critical_radius_bisection(rho_ext, R_shrink, R_grow, fate=None, **run_kw):
+    """Sec. III A's estimate of the lattice's critical radius: the smallest
+    seed radius R_g that grows and the largest R_s that shrinks, one node
+    apart, give R_c = (R_g + R_s) / 2.  Integer seed radii (nodes) are
+    bisected between a bracket R_shrink < R_grow that must shrink and grow;
+    `fate(R0)` classifies one seed (default: a bubble_in_reservoir run with
+    `run_kw`, judged by bubble_fate; an undecided run raises).  Returns
+    (R_s, R_g, R_c, {R0: fate}) in nodes."""
+    if fate is None:
+        def fate(R0):
+            return bubble_fate(bubble_in_reservoir(R0, rho_ext, **run_kw))
+    lo, hi = int(R_shrink), int(R_grow)
+    if not lo < hi:
+        raise ValueError("need R_shrink < R_grow")
+    seen = {}
+    for r, want in ((lo, -1), (hi, 1)):
+        seen[r] = fate(r)
+        if seen[r] != want:
+            raise ValueError(f"seed {r} does not {'shrink' if want < 0 else 'grow'} "
+                             f"(fate {seen[r]}): widen the bracket or the run")
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        seen[mid] = fate(mid)
+        if seen[mid] == 0:
+            raise ValueError(f"seed {mid} undecided: lengthen the run")
+        if seen[mid] > 0:
+            hi = mid
+        else:
+            lo = mid
+    return lo, hi, 0.5 * (lo + hi), seen
 
 
 def rp_prediction(run: BubbleRun, t0: float, sigma=None, window=0.5):

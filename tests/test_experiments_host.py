@@ -43,3 +43,35 @@ def test_bubble_fields_geometry():
     assert abs(rho[48, 64] - 0.24) < 1e-9 and abs(rho[0, 0] - 1.9) < 1e-9
     nb = (rho < 0.5 * (0.24 + 1.9)).sum()
     assert abs(math.sqrt(nb / math.pi) - 20.0) < 0.5
+
+
+def test_critical_radius_bisection_logic():
+    """Sec. III A's estimate R_c = (R_g + R_s)/2 with R_g = R_s + 1 node, on a
+    stand-in classifier (the GPU run is replaced by a threshold at 76.3)."""
+    import pytest
+    from paper_1802_01272_gb300 import experiments as X
+    calls = []
+
+    def fate(r):
+        calls.append(r)
+        return 1 if r > 76.3 else -1
+    rs, rg, rc, seen = X.critical_radius_bisection(1.923, 60, 100, fate=fate)
+    assert (rs, rg, rc) == (76, 77, 76.5)
+    assert len(calls) <= 2 + 6 and seen[76] == -1 and seen[77] == 1
+    with pytest.raises(ValueError):
+        X.critical_radius_bisection(1.923, 80, 100, fate=fate)     # 80 grows
+    with pytest.raises(ValueError):
+        X.critical_radius_bisection(1.923, 60, 100, fate=lambda r: 0 if r == 80 else fate(r))
+
+
+def test_bubble_fate_reads_growth_after_relaxation():
+    from paper_1802_01272_gb300 import experiments as X
+    from paper_1802_01272_gb300.binding import Params
+    t = np.arange(0.0, 8.01, 0.5)
+    p = Params(Lx=64, Ly=64, ds=1 / 256)
+    mk = lambda R: X.BubbleRun(t=t, R=np.asarray(R) / 256, rho_center=t * 0, rho_inf=t * 0,  # noqa: E731
+                               r_inf=1.0, params=p)
+    dip = np.where(t < 1.0, 80 - 5 * t, 75 + 0.5 * (t - 1.0))   # relaxes down, then grows
+    assert X.bubble_fate(mk(dip)) == 1
+    assert X.bubble_fate(mk(80 - 0.9 * t)) == -1
+    assert X.bubble_fate(mk(80 + 0.01 * t)) == 0

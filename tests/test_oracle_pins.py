@@ -379,6 +379,29 @@ def test_force_stencils_exact_on_polynomials(oracle_mod):
     assert err < 1e-9
 
 
+def test_oracle_planar_vapour_density_at_T06_against_paper(oracle_mod):
+    """Sec. II E: on the paper's grid (CTU2, tau = 1e-3, dt = 1e-4,
+    ds = 1/256) the planar interface's vapour density at T = 0.6 sits about
+    8 % under the Maxwell value.  The oracle's relaxed slab (48 nodes, one
+    row, t = 3, converged to 4e-4): -9.9 %, liquid within 2e-3.  The 3x3
+    pressure gradient gives -30 % here."""
+    from oracle import analysis as A
+    O = oracle_mod
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                    "paper_values.json")))["phase_diagram_vapour_deviation"]
+    T = g["T_low"]
+    rl, rv = A.maxwell(T)
+    Lx = 48
+    x = np.arange(Lx, dtype=np.float64)
+    prof = rv + 0.5 * (rl - rv) * (np.tanh((x - Lx / 4) / 2.0) - np.tanh((x - 3 * Lx / 4) / 2.0))
+    p = params(O, Lx=Lx, Ly=1, T=T, tau=1e-3, dt=1e-4, ds=1 / 256)
+    f = O.init_feq(p, prof[None, :], np.zeros((1, Lx)), np.zeros((1, Lx)))
+    r, _, _ = O.moments(p, O.step(p, f, 30000))
+    dev_v, dev_l = 1.0 - r.min() / rv, r.max() / rl - 1.0
+    print(f"\nT={T}: rho_V {-dev_v:+.3e} rho_L {dev_l:+.3e} of Maxwell (paper: about -{g['vapour_rel_diff_at_T_low']})")
+    assert abs(dev_v - g["vapour_rel_diff_at_T_low"]) < 0.04 and abs(dev_l) < 2e-3
+
+
 # ------------------------------------------------------ boundaries (Sec. III)
 def test_reservoir_sets_outside_density(oracle_mod):
     O = oracle_mod

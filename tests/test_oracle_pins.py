@@ -402,6 +402,28 @@ def test_oracle_planar_vapour_density_at_T06_against_paper(oracle_mod):
     assert abs(dev_v - g["vapour_rel_diff_at_T_low"]) < 0.04 and abs(dev_l) < 2e-3
 
 
+def test_oracle_planar_surface_tension_against_paper(oracle_mod):
+    """Sec. III A: sigma of the relaxed planar interface at T = 0.8,
+    kappa = 1e-4, ds = 1/256, tau = 1e-3 is 4.8747e-3 (Eq. sigma, summed as
+    kappa sum (centred difference)^2 ds per interface).  The oracle's 80-node
+    slab at t = 6: +0.06 % (t = 8: +0.04 %)."""
+    from oracle import analysis as A
+    O = oracle_mod
+    want = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "paper_values.json")))["surface_tension_T0.8_kappa1e-4"]["ds_1_256"]
+    rl, rv = A.maxwell(0.8)
+    Lx, ds = 80, 1 / 256
+    x = np.arange(Lx, dtype=np.float64)
+    prof = rv + 0.5 * (rl - rv) * (np.tanh((x - Lx / 4) / 2.0) - np.tanh((x - 3 * Lx / 4) / 2.0))
+    p = params(O, Lx=Lx, Ly=1, T=0.8, tau=1e-3, dt=1e-4, ds=ds, kappa=1e-4)
+    f = O.init_feq(p, prof[None, :], np.zeros((1, Lx)), np.zeros((1, Lx)))
+    r = O.moments(p, O.step(p, f, 60000))[0][0]
+    grad = (np.roll(r, -1) - np.roll(r, 1)) / (2 * ds)
+    sigma = p.kappa * float(np.sum(grad * grad)) * ds / 2
+    print(f"\nsigma {sigma:.6e} (paper {want:.6e}, rel {(sigma - want) / want:+.2e})")
+    assert abs(sigma - want) / want < 5e-3
+
+
 # ------------------------------------------------------ boundaries (Sec. III)
 def test_reservoir_sets_outside_density(oracle_mod):
     O = oracle_mod

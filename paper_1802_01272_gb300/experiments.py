@@ -1,7 +1,8 @@
 """Bubble experiments of Sec. III run on the CUDA path.
 
 * surface tension of a relaxed planar interface, sigma = kappa int (d rho/dx)^2 dx
-  (Eq. sigma, in the reading whose values the paper prints);
+  (Eq. sigma, in the reading whose values the paper prints), and the
+  liquid-vapour phase diagram from such interfaces (Sec. II E);
 * the critical radius of Eq. (raggio_c) and the growth or collapse of bubbles
   around it with the density reservoir of Sec. III A, and the lattice's own
   critical radius by bisection on the seed radius as Sec. III A estimates it;
@@ -99,6 +100,22 @@ def planar_interface_sigma(T=0.8, kappa=1e-4, ds=1 / 256, Lx=512, Ly=8, tau=1e-3
     prof = r.mean(axis=0)
     grad = (np.roll(prof, -1) - np.roll(prof, 1)) / (2.0 * ds)
     return kappa * float(np.sum(grad * grad)) * ds / 2.0, prof
+
+
+def phase_diagram(temperatures, kappa=1e-4, ds=1 / 256, tau=1e-3, Lx=128, t_end=20.0,
+                  precision=LBM_FP32_SHIFTED, stream=None):
+    """Sec. II E's liquid-vapour phase diagram from relaxed planar interfaces:
+    for each T, the liquid and vapour plateau densities of a slab (periodic x,
+    `Lx` nodes, relaxed to t_end) beside the Maxwell values.  Returns a list of
+    dicts with T, rho_L, rho_V, maxwell_L, maxwell_V and sigma."""
+    out = []
+    for T in temperatures:
+        sigma, prof = planar_interface_sigma(T=T, kappa=kappa, ds=ds, Lx=Lx, tau=tau,
+                                             t_end=t_end, precision=precision, stream=stream)
+        rl, rv = eos.coexistence(T)
+        out.append({"T": float(T), "rho_L": float(prof.max()), "rho_V": float(prof.min()),
+                    "maxwell_L": rl, "maxwell_V": rv, "sigma": sigma})
+    return out
 
 
 @dataclass

@@ -75,3 +75,25 @@ def test_bubble_fate_reads_growth_after_relaxation():
     assert X.bubble_fate(mk(dip)) == 1
     assert X.bubble_fate(mk(80 - 0.9 * t)) == -1
     assert X.bubble_fate(mk(80 + 0.01 * t)) == 0
+
+
+def test_phase_diagram_driver_plumbing(monkeypatch):
+    """phase_diagram runs one planar interface per temperature with the given
+    grid and pairs its plateaus with the Maxwell densities (the lattice run
+    itself is replaced by a stand-in profile here; the GPU tests run it)."""
+    from paper_1802_01272_gb300 import eos
+    from paper_1802_01272_gb300 import experiments as X
+    seen = []
+
+    def fake(T, kappa, ds, Lx, tau, t_end, precision, stream):
+        seen.append((T, kappa, ds, Lx, tau, t_end))
+        rl, rv = eos.coexistence(T)
+        return 1e-3 * T, np.array([rv * 0.9, rl, rv * 0.9])
+    monkeypatch.setattr(X, "planar_interface_sigma", fake)
+    rows = X.phase_diagram((0.6, 0.8), Lx=96, t_end=5.0)
+    assert [r["T"] for r in rows] == [0.6, 0.8]
+    assert seen == [(0.6, 1e-4, 1 / 256, 96, 1e-3, 5.0), (0.8, 1e-4, 1 / 256, 96, 1e-3, 5.0)]
+    for r in rows:
+        rl, rv = eos.coexistence(r["T"])
+        assert r["maxwell_L"] == rl and r["maxwell_V"] == rv
+        assert r["rho_L"] == rl and abs(r["rho_V"] / rv - 0.9) < 1e-12

@@ -40,7 +40,9 @@ struct lbm_handle {
   double xi[16][2], w[16];
   StepArgs<float> a32;
   StepArgs<double> a64;
-  RowMaps tmap[2];  // tensor maps of f[0], f[1] (RPI-row and 1-row boxes)
+  // tensor maps of the step from f[c] to f[1 - c]: loads of f[c] (RPI-row and
+  // 1-row staging boxes), stores into f[1 - c] (RPI-row and 1-row output tiles)
+  RowMaps tmap[2];
   // CUDA graphs of GRAPH_STEPS consecutive steps starting from f[0] / f[1]
   // (built on first use, rebuilt when the launch geometry changes)
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -91,17 +93,18 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// f [16][Ly][Lx] as a 3-D tensor ordered (x, plane, row), read in boxes of
-// SCOL columns x 16 planes x `rows` rows: the box lands in shared memory as
-// `rows` consecutive staged rows [16][SCOL].  False when the encoder is
-// unavailable or rejects the layout (the kernel then stages every strip by
-// per-thread copies).
-bool encode_row_map(void* base, size_t elem, int Lx, int Ly, int rows, CUtensorMap* out) {
+// f [16][Ly][Lx] as a 3-D tensor ordered (x, plane, row), moved in boxes of
+// `cols` columns x 16 planes x `rows` rows: a box is [rows][16][cols] in
+// shared memory (the staging ring's rows, or the collision's output tile).
+// False when the encoder is unavailable or rejects the layout (the kernel then
+// stages every strip by per-thread copies, or stores per thread).
+bool encode_row_map(void* base, size_t elem, int Lx, int Ly, int cols, int rows,
+                    CUtensorMap* out) {
   const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc || Lx < SCOL || Ly < rows) return false;
+  if (!enc || Lx < cols || Ly < rows) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)Lx, 16, (cuuint64_t)Ly};
   const cuuint64_t strides[2] = {(cuuint64_t)Lx * (cuuint64_t)Ly * elem, (cuuint64_t)Lx * elem};
-  const cuuint32_t box[3] = {(cuuint32_t)SCOL, 16, (cuuint32_t)rows};
+  const cuuint32_t box[3] = {(cuuint32_t)cols, 16, (cuuint32_t)rows};
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUtensorMapDataType type = elem == 8   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                    : elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
@@ -124,12 +127,11 @@ int cuda_check(lbm_handle* h, cudaError_t e) {
 
 double rho_ref_of(const lbm_params& p) { return p.precision == LBM_FP64 ? 0.0 : p.rho_ref; }
 
-// FP32 keeps the relaxation and the corner weights exactly balanced: omega and
-// the off-corner weights are put on the 2^-24 grid, so that 1 - omega and
-// c00 = 1 - c10 - c01 - c11 are exact in FP32.  Rounding them separately would
-// leave (1 - omega) + omega and the weight sum 2e-8 off 1, a systematic damping
-// of every deviation by that much per step (it shows as +2% in the decay rate
-// of a shear wave over 2e5 steps).  FP64 keeps the exact values.
+// FP32 keeps the relaxation exactly balanced: omega is put on the 2^-24 grid,
+// so that 1 - omega is exact in FP32.  Rounding the two separately would leave
+// (1 - omega) + omega 2e-8 off 1, a systematic damping of every deviation by
+// that much per step (it shows as +2% in the decay rate of a shear wave over
+// 2e5 steps).  FP64 keeps the exact value.
 double snap(double v, bool fp32) {
   return fp32 ? std::ldexp(std::nearbyint(std::ldexp(v, 24)), -24) : v;
 }
@@ -156,10 +158,18 @@ void fill_step_args(lbm_handle* h, StepArgs<T>& a) {
   a.Tt = (T)p.T;
   a.a = (T)p.a;
   a.b = (T)p.b;
-  a.kappa = (T)p.kappa;
-  a.inv_ds = (T)(1.0 / p.ds);
-  a.inv_ds2 = (T)(1.0 / (p.ds * p.ds));
-  a.dt = (T)p.dt;
+  // force stencils (Eq. eder): the fourth-order gradient (4 D_h - D_2h)/3 of
+  // p^i - p^w and the isotropic gradient D_h of the 9-point Laplacian, with
+  // dt/ds (and kappa) folded into the weights
+  a.gw1 = (T)(4.0 / 9.0 * lam);
+  a.gw2 = (T)(1.0 / 9.0 * lam);
+  a.gw3 = (T)(1.0 / 18.0 * lam);
+  a.gw4 = (T)(1.0 / 72.0 * lam);
+  a.lw1 = (T)(1.0 / 3.0 * p.kappa * lam);
+  a.lw2 = (T)(1.0 / 12.0 * p.kappa * lam);
+  a.lp1 = (T)(2.0 / 3.0 / (p.ds * p.ds));
+  a.lp2 = (T)(1.0 / 6.0 / (p.ds * p.ds));
+  a.lp0 = (T)(10.0 / 3.0 / (p.ds * p.ds));
   a.omega = (T)om;
   a.one_m_omega = (T)(1.0 - om);
   a.om2 = (T)(0.5 * om);
@@ -198,22 +208,17 @@ void fill_step_args(lbm_handle* h, StepArgs<T>& a) {
     v.xi_x = (T)x;
     v.xi_y = (T)y;
     v.w = (T)h->w[k];
-    const double c10 = snap(cx * (1.0 - cy), f32), c01 = snap(cy * (1.0 - cx), f32);
-    const double c11 = snap(cx * cy, f32);
-    v.c00 = (T)(1.0 - c10 - c01 - c11);
-    v.c10 = (T)c10;
-    v.c01 = (T)c01;
-    v.c11 = (T)c11;
-    // U2 = -lam hx [(1-cy) dS^x + cy dS^x(j - sgn_y)] - lam hy [(1-cx) dS^y + cx dS^y(i - sgn_x)],
-    // with the kernel's half-limited jumps (hence the factor 2)
-    v.a1 = (T)(2.0 * lam * hx * (1.0 - cy));
-    v.a2 = (T)(2.0 * lam * hx * cy);
-    v.b1 = (T)(2.0 * lam * hy * (1.0 - cx));
-    v.b2 = (T)(2.0 * lam * hy * cx);
-    v.omA = (T)(om * Ak);
-    v.Ak = (T)Ak;
-    v.omB = (T)(om * Bk);
-    v.Bk = (T)Bk;
+    // CTU2 per node (Sec. II C 2 collected): with Z(j) = f - c_x (f - f(i - s_x))
+    // - 2 lam hx dS^x(j), the update is Z(j) + c_y (Z(j - s_y) - Z(j))
+    // - 2 lam hy [(1 - c_x) dS^y(i) + c_x dS^y(i - s_x)] on the kernel's
+    // half-limited jumps (hence the factors 2).  The interpolations
+    // f + c (g - f) return f exactly for g = f, so the CTU1 weights of a
+    // uniform state sum to 1 in any precision.
+    v.cx = (T)cx;
+    v.cy = (T)cy;
+    v.ax = (T)(2.0 * lam * hx);
+    v.by0 = (T)(-2.0 * lam * hy * (1.0 - cx));
+    v.by1 = (T)(-2.0 * lam * hy * cx);
     v.gbot = (T)(gb[k] - h->w[k] * rr);
     v.gtop = (T)(gt[k] - h->w[k] * rr);
     // Eq. (ereg): w [ H2:A2 / 2! + H3:A3 / 3! ] over the independent components
@@ -403,12 +408,16 @@ int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out) {
   else
     fill_step_args<float>(h, h->a32);
   std::memset(h->tmap, 0, sizeof(h->tmap));
-  bool tma = h->vec;
-  for (int i = 0; i < 2 && tma; ++i)
-    tma = encode_row_map(h->f[i], h->elem, p->Lx, p->Ly, RPI, &h->tmap[i].m[0]) &&
-          encode_row_map(h->f[i], h->elem, p->Lx, p->Ly, 1, &h->tmap[i].m[1]);
-  h->a32.tma_ok = tma;
-  h->a64.tma_ok = tma;
+  bool tin = h->vec, tout = h->vec;
+  for (int i = 0; i < 2; ++i) {
+    tin = tin && encode_row_map(h->f[i], h->elem, p->Lx, p->Ly, SCOL, RPI, &h->tmap[i].m[0]) &&
+          encode_row_map(h->f[i], h->elem, p->Lx, p->Ly, SCOL, 1, &h->tmap[i].m[1]);
+    tout = tout &&
+           encode_row_map(h->f[1 - i], h->elem, p->Lx, p->Ly, TW, RPI, &h->tmap[i].m[2]) &&
+           encode_row_map(h->f[1 - i], h->elem, p->Lx, p->Ly, TW, 1, &h->tmap[i].m[3]);
+  }
+  h->a32.tma_in = h->a64.tma_in = tin;
+  h->a32.tma_out = h->a64.tma_out = tout;
   AuxArgs& x = h->aux;
   x.Lx = p->Lx;
   x.Ly = p->Ly;
@@ -746,7 +755,7 @@ int lbm_step_many(lbm_handle* const* handles, int32_t count, int64_t n) {
     }
     std::unique_ptr<BatchArgs<float>> bp(new (std::nothrow) BatchArgs<float>());
     if (!bp) return set_err(h0, LBM_ERR_OOM);
-    BatchArgs<float>& b = *bp;  // ~31 KB, copied into the launch's parameter space
+    BatchArgs<float>& b = *bp;  // ~23 KB, copied into the launch's parameter space
     long long total = 0;
     b.count = ng;
     b.sched = h0->d_sched;
@@ -771,6 +780,7 @@ int lbm_step_many(lbm_handle* const* handles, int32_t count, int64_t n) {
         b.L[i].items = its[i];
         b.L[i].fin = static_cast<const float*>(h->f[h->cur]);
         b.L[i].fout = static_cast<float*>(h->f[1 - h->cur]);
+        b.maps[i] = h->tmap[h->cur];
       }
       cudaError_t e = launch_step_batch_f32(b, h0->p.ctu_order, lim0, true, g, group[0]->smem,
                                             h0->stream);
@@ -912,7 +922,7 @@ int lbm_get_kernel_info(const lbm_handle* h, lbm_kernel_info* out) {
   out->smem_bytes = (int32_t)h->smem;
   out->strips = h->nstrip;
   out->row_block = h->row_block;
-  out->tensor_copies = h->elem == 8 ? h->a64.tma_ok : h->a32.tma_ok;
+  out->tensor_copies = h->elem == 8 ? h->a64.tma_in : h->a32.tma_in;
   return LBM_OK;
 }
 

@@ -286,10 +286,12 @@ cudaError_t launch_hist(const AuxArgs& a, const void* f, int nbins, double lo, d
 
 size_t step_smem_bytes(size_t stage_elem, size_t elem) {
   const size_t elems = (size_t)FROWS * 16 * REG + 6 * (size_t)MROWS * REG;
-  // + 128 bytes to align the staging ring for tensor copies; ints, the fused
-  // diagnostics' bubble-site sums, two mbarriers and the CTA's wait-abort flag
-  return 128 + stage_elem * SROWS * 16 * SCOL + elem * elems + sizeof(int) * (SG + (SG & 1)) +
-         6 * sizeof(unsigned long long) + 2 * sizeof(unsigned long long) + 2 * sizeof(int);
+  // + 128 bytes to align the staging ring and the output tiles for tensor
+  // copies; ints, the fused diagnostics' bubble-site sums, two mbarriers and
+  // the CTA's wait-abort flag
+  return 128 + stage_elem * ((size_t)SROWS * 16 * SCOL + 2 * (size_t)RPI * 16 * TW) +
+         elem * elems + sizeof(int) * (SG + (SG & 1)) + 6 * sizeof(unsigned long long) +
+         2 * sizeof(unsigned long long) + 2 * sizeof(int);
 }
 
 }  // namespace ctulbm

@@ -10,28 +10,25 @@
 // Sec. III A.
 //
 // Kernel layout (step_kernel): a CTA owns a strip of TW = 56 output columns
-// [56 s, 56 s + 56) and streams down a range of rows, RPI = 4 rows per
-// iteration.  Its 256 threads are (velocity k, group g of four columns) over a
-// 64-column region [56 s - 4, 56 s + 60): the strip, the two-column halo where
-// rho* is needed for the force stencil, and two more columns that complete the
-// four-column groups.  Strips start on 32-byte sectors, so every output sector
-// is written whole by one warp store (a partly written sector would cost a
-// DRAM read-modify-write).  Warps hold one sign quadrant (sgn xi_x, sgn xi_y), so
-// the upwind side of every stencil is a compile-time constant inside a warp.
-// Per iteration of four rows a0 .. a0+3 the CTA
-//   L   issues cp.async copies of the f^n rows of the NEXT iteration into a
-//       shared staging ring (one iteration of look-ahead hides DRAM latency);
-//   P1  advects rows a0..a0+3 of every plane from the staging ring (the CTU2
-//       jumps, limited corrections and their differences of the previous rows
-//       live in registers) into a ring of advected rows f*;
-//   P2  one thread per node: rho*, u*, p^i - p^w of rows a0..a0+3;
-//   P3  one thread per node: 9-point Laplacian of rho* on rows a0-1..a0+2;
-//   P4  one thread per node on rows a0-2..a0+1: gradients (5x5 of p^i - p^w,
-//       3x3 of the Laplacian) -> g, the collision coefficients, then all 16
-//       planes relaxed and stored
-//       (coalesced 128-byte warp stores per plane).
-// Four CTA barriers per four rows.  Global memory is read once per step for
-// f^n (halo columns of neighbouring strips are L2 hits) and written once.
+// [56 s, 56 s + 56) and streams down a range of rows, 4 rows per iteration.
+// Its 256 threads are (velocity k, group g of four columns) over a 64-column
+// region [56 s - 4, 56 s + 60): the strip, the two columns of rho* halo the
+// force stencil needs on each side, and two more that complete the groups.
+// Warps hold one sign quadrant (sgn xi_x, sgn xi_y), so the upwind side of
+// every stencil is a compile-time constant inside a warp.  Iteration i takes
+// the staged rows n = B_i .. B_i + 3 of f^n (one tensor copy of 72 columns x
+// 16 planes x 4 rows, issued one iteration ahead into a two-slot ring) and
+//   P1  advects them (every quadrant emits the rows n - 2, two rows behind
+//       the staged one) into a ring of advected rows f*;
+//   P2  one thread per node: rho*, u*, p^i - p^w of those rows;
+//   P3  the 9-point Laplacian of rho* one row further back;
+//   P4  224 threads, one per output node, two rows further back: gradients
+//       -> g, f^eq + dt F_k, relaxation of all 16 planes into an output tile
+//       that one thread writes to f^{n+1} with a tensor store.
+// Four CTA barriers per four rows; every shared-memory offset inside an
+// iteration is a compile-time constant from a per-thread base.  f^n is read
+// from HBM once per step (the halo columns of neighbouring strips are L2
+// hits) and f^{n+1} written once.
 #pragma once
 
 #include <cuda.h>  // CUtensorMap (type only)
@@ -46,22 +43,22 @@ constexpr int REG = 4 * NG;     // region columns: output strip plus 4 columns p
 constexpr int TW = REG - 8;     // output columns per strip (56: strips start on 32-byte sectors)
 constexpr int XOFF = 4;         // region column of the strip's first output column
 constexpr int NT = 16 * NG;     // threads per CTA
-constexpr int RPI = 4;          // rows per pipeline iteration
+constexpr int RPI = 4;          // rows per pipeline iteration (one staged batch)
 constexpr int SG = NG + 2;      // staging groups per plane row: region plus one group per side
 constexpr int SCOL = 4 * SG;    // staging columns per plane row
-constexpr int SROWS = 3 * RPI;  // staging ring rows: three batches of RPI rows (the batch read,
-                                // the last row of the one before, the batch being loaded)
-constexpr int FROWS = 8;        // advected-row ring (power of two)
+constexpr int SROWS = 2 * RPI;  // staging ring: the batch being read and the one being loaded
+constexpr int FROWS = 8;        // advected-row ring f* (power of two)
 constexpr int MROWS = 8;        // moment rings (power of two)
-constexpr int WARMUP = 5;       // pipeline rows before the first output row of a segment
+constexpr int P4T = RPI * TW;   // collision threads: one per output node of an iteration
+constexpr int WARM = 2;         // iterations of a segment before its first output row
 
 // Per-velocity constants, computed on the host in FP64 and rounded to T.
 template <typename T>
 struct VelConst {
   T xi_x, xi_y, w;
-  T c00, c10, c01, c11;     // Eq. (ctueq) corner weights (1-cx)(1-cy), cx(1-cy), cy(1-cx), cx cy
-  T a1, a2, b1, b2;         // CTU2 correction weights acting on half-limited jumps
-  T omA, Ak, omB, Bk;       // omega*A_k, A_k, omega*B_k, B_k; A_k=(T-1)(xi^2-2)/2, B_k=(T-1)(xi^2-4)/2
+  T cx, cy;                 // Courant numbers |xi_x| dt/ds, |xi_y| dt/ds
+  T ax;                     // lam |xi_x| (1 - cx): weight of the x-difference of half-limited S^x
+  T by0, by1;               // -lam |xi_y| (1 - cy) (1 - cx), -lam |xi_y| (1 - cy) cx (S^y terms)
   T gbot, gtop;             // wall ghost-row values (storage variable)
   T r2xx, r2xy, r2yy, r3xxx, r3xxy, r3xyy, r3yyy;  // Eq. (ereg) weights, 1/n! folded in
 };
@@ -88,22 +85,29 @@ struct StepArgs {
   unsigned long long* diag_sums;  // [6]: nb, sx, sy, sxx, sxy, syy
   T diag_thr;
   int walls, reservoir, regularize;
-  T rho_ref, Tt, a, b, kappa, inv_ds, inv_ds2, dt, omega, one_m_omega, om2, om6;
+  T rho_ref, Tt, a, b, omega, one_m_omega, om2, om6;
+  // force stencils with dt/ds (and kappa) folded in: g dt/ds = ir * (gradient
+  // of p^i - p^w) + kappa * (gradient of the Laplacian)
+  T gw1, gw2, gw3, gw4;     // (4/9, 1/9, 1/18, 1/72) dt/ds
+  T lw1, lw2;               // (1/3, 1/12) kappa dt/ds
+  T lp1, lp2, lp0;          // 9-point Laplacian: (2/3, 1/6, 10/3) / ds^2
   T rho_ext, rbc2, cxc, cyc;
   unsigned int* err;         // bit 0: non-finite or non-positive rho; bit 1: a wait timed out
-  int tma_ok;               // the launch's tensor map describes fin (interior strips use it)
+  int tma_in;               // the tensor maps describe fin (interior strips stage by tensor copies)
+  int tma_out;              // the store maps describe fout (tiles leave by tensor stores)
   T xlo, xhi;               // |xi| components sqrt(3 - sqrt 6), sqrt(3 + sqrt 6)
   ClassConst<T> cls[4];     // groups (lo,lo), (hi,lo), (lo,hi), (hi,hi)
   VelConst<T> v[16];
 };
 
-// f^n as a 3-D tensor (x, plane, row) for tensor copies of staged rows:
-// m[0] copies boxes of SCOL columns x 16 planes x RPI rows, m[1] single rows.
+// f^n and f^{n+1} as 3-D tensors (x, plane, row): m[0] loads boxes of SCOL
+// columns x 16 planes x RPI rows of fin, m[1] single rows; m[2] stores boxes
+// of TW columns x 16 planes x RPI rows into fout, m[3] single rows.
 struct RowMaps {
-  CUtensorMap m[2];
+  CUtensorMap m[4];
 };
 
-constexpr int MAXB = 16;  // lattices per batched launch (kernel parameter space)
+constexpr int MAXB = 12;  // lattices per batched launch (kernel parameter space)
 
 template <typename T>
 struct BatchArgs {
@@ -111,6 +115,7 @@ struct BatchArgs {
   unsigned long long* sched;       // [2] work counter and done counter
   long long item_start[MAXB + 1];  // prefix sums of the lattices' work items
   StepArgs<T> L[MAXB];
+  RowMaps maps[MAXB];
 };
 
 // ---------------------------------------------------------------- helpers
@@ -132,20 +137,11 @@ template <>
 __device__ __forceinline__ __half to_store<__half, float>(float v) {
   return __float2half_rn(v);
 }
-__device__ __forceinline__ float flip_sign(float v, float s) {
-  return __int_as_float(__float_as_int(v) ^ (__float_as_int(s) & 0x80000000));
-}
 __device__ __forceinline__ double flip_sign(double v, double s) {
   return __longlong_as_double(__double_as_longlong(v) ^
                               (__double_as_longlong(s) & (long long)0x8000000000000000ULL));
 }
 
-__device__ __forceinline__ float min3(float a, float b, float c) {
-  float r;
-  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-  return r;
-}
-__device__ __forceinline__ double min3(double a, double b, double c) { return fmin(fmin(a, b), c); }
 // Reciprocal in FP32: the hardware approximation (relative error below 2^-22),
 // enough for u = (rho u)/rho and the pressure and force terms, which enter the
 // update multiplied by dt; FP64 keeps the correctly rounded division.
@@ -156,20 +152,43 @@ __device__ __forceinline__ float rcp(float x) {
 }
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 
-// Half of the limited jump R * Psi(Ru / R) of Sec. II C 2.  For the MC limiter,
-// with a = |R| and b = sgn(R) Ru, R Psi = sgn(R) max(0, min((a+b)/2, 2a, 2b)),
-// which needs no division and is 0 at R = 0 (where Psi's argument is undefined).
-template <int LIM, typename T>
-__device__ __forceinline__ T half_limited(T R, T Ru) {
+// min(|a|, |b|) carrying the sign sgn(a) sgn(b) (one instruction on sm_86+).
+__device__ __forceinline__ float min_xorsign_abs(float a, float b) {
+  float r;
+  asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+
+// Half of the limited jump R Psi(Ru / R) of Sec. II C 2 (Ru the upwind jump).
+// For the MC limiter Psi = max(0, min((1 + th)/2, 2, 2 th)) this is the
+// three-way minmod of R, Ru and (R + Ru)/4: the one of least magnitude when
+// all three share a sign, else 0 -- no division, and 0 at R = 0 where the
+// limiter's argument is undefined.  FP32: u = minmod(R, Ru) as sgn(R) sgn(Ru)
+// min(|R|, |Ru|) clamped at 0, then min(u, |h|) with the sign of h = (R + Ru)/4,
+// which is sgn(R) whenever u > 0.
+template <int LIM>
+__device__ __forceinline__ float half_limited(float R, float Ru) {
   if constexpr (LIM == 1) {
-    return T(0);
+    return 0.0f;
   } else if constexpr (LIM == 2) {
-    return T(0.5) * R;
+    return 0.5f * R;
   } else {
-    T a = fabs(R);
-    T b = flip_sign(Ru, R);
-    T m = min3(T(0.25) * (a + b), a, b);
-    m = fmax(m, T(0));
+    const float h = 0.25f * (R + Ru);
+    const float u = fmaxf(min_xorsign_abs(R, Ru), 0.0f);
+    return min_xorsign_abs(u, h);
+  }
+}
+template <int LIM>
+__device__ __forceinline__ double half_limited(double R, double Ru) {
+  if constexpr (LIM == 1) {
+    return 0.0;
+  } else if constexpr (LIM == 2) {
+    return 0.5 * R;
+  } else {
+    const double a = fabs(R);
+    const double b = flip_sign(Ru, R);  // sgn(R) Ru
+    double m = fmin(fmin(0.25 * (a + b), a), b);
+    m = fmax(m, 0.0);
     return copysign(m, R);
   }
 }
@@ -179,52 +198,62 @@ __device__ __forceinline__ int wrapi(int i, int n) {
   return r < 0 ? r + n : r;
 }
 
-template <typename T>
-__device__ __forceinline__ void sload4(const T* p, T* v) {
-  if constexpr (sizeof(T) == 4) {
-    float4 t = *reinterpret_cast<const float4*>(p);
-    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-  } else {
-    double2 t0 = reinterpret_cast<const double2*>(p)[0];
-    double2 t1 = reinterpret_cast<const double2*>(p)[1];
-    v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
-  }
-}
-
-// Twelve consecutive staged values (16-byte aligned for float/double, 8-byte
-// for half) converted to the arithmetic type.
-template <typename S, typename T>
-__device__ __forceinline__ void sload12(const S* p, T* v) {
-  if constexpr (sizeof(S) == 2) {
+// n consecutive staged values from shared memory (16-byte aligned start for
+// n = 4, 8-byte for n = 2; half: 8- and 4-byte), converted to T.
+template <typename S, typename T, int N>
+__device__ __forceinline__ void sload(const S* p, T* v) {
+  if constexpr (sizeof(S) == 4) {
+    if constexpr (N == 4) {
+      const float4 t = *reinterpret_cast<const float4*>(p);
+      v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else if constexpr (N == 2) {
+      const float2 t = *reinterpret_cast<const float2*>(p);
+      v[0] = t.x; v[1] = t.y;
+    } else {
+      v[0] = *p;
+    }
+  } else if constexpr (sizeof(S) == 8) {
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      const uint2 u = reinterpret_cast<const uint2*>(p)[m];
+    for (int m = 0; m < N / 2; ++m) {
+      const double2 t = reinterpret_cast<const double2*>(p)[m];
+      v[2 * m] = t.x; v[2 * m + 1] = t.y;
+    }
+    if constexpr (N & 1) v[N - 1] = p[N - 1];
+  } else {
+    if constexpr (N == 4) {
+      const uint2 u = *reinterpret_cast<const uint2*>(p);
       const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
       const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
-      v[4 * m] = a.x; v[4 * m + 1] = a.y; v[4 * m + 2] = b.x; v[4 * m + 3] = b.y;
+      v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    } else if constexpr (N == 2) {
+      const float2 a = __half22float2(*reinterpret_cast<const __half2*>(p));
+      v[0] = a.x; v[1] = a.y;
+    } else {
+      v[0] = __half2float(*p);
     }
-  } else {
-    sload4(p, v);
-    sload4(p + 4, v + 4);
-    sload4(p + 8, v + 8);
   }
 }
 
 // ------------------------------------------------------ advection state
-// Columns: the thread owns group columns 0..3.  f keeps five columns C5 =
-// {own, own - sgn_x} (relative -1..3 for sgn_x > 0, else 0..4), loaded from
-// the staged row.  Jumps, limited corrections and their differences are kept
-// for the own four columns only: the value a stencil needs one column beyond
-// the group is the neighbouring group's, taken from the adjacent lane (the 16
-// groups of a velocity sit on 16 consecutive lanes).  At the two region edges
-// that lane holds nothing useful; those columns (region 0 and 63) feed only
-// rho* outside the stencils of the strip's outputs.
+// A thread advects four columns of one plane.  Row history, for its own
+// columns: f and R^y of the last staged row, the last S^y, and Z of the last
+// two rows, Z = f - c_x (f - f_upwind) - ax dS^x the x part of the update
+// (CTU1's x-weights and the limited x correction in one number per node).
+// Output row j = Z(j) + c_y (Z(j - s_y) - Z(j)) + by0 dS^y(i) + by1 dS^y(i - s_x),
+// with dS^x = S^x(i+1) - S^x(i), dS^y = S^y(j+1) - S^y(j) (Sec. II C 2,
+// collected per node).  A value a stencil needs one column beyond the group
+// is the neighbouring group's, taken from the adjacent lane (a velocity's 16
+// groups sit on 16 consecutive lanes).  At the two region edges that lane
+// holds nothing useful; those columns (region 0 and 63) feed only rho*
+// outside the stencils of the strip's outputs.
 template <typename T>
 struct AdvState {
-  T F0[5], F1[5];  // f on row a and on the y-upwind row a - sgn_y
-  T RY[4];         // sgn_y > 0: R^y(a);  sgn_y < 0: R^y(a+1)
-  T SY[4];         // half-limited S^y(a)
-  T A0[4], A1[4];  // x-differences of half-limited S^x on row a and on row a - sgn_y
+  T Fp[4];   // f(n - 1)
+  T Ryp[4];  // R^y(n - 1)
+  T Syp[4];  // s_y > 0: S^y(n - 1);  s_y < 0: S^y(n - 2)
+  T Z1[4];   // Z(n - 1)
+  T Z2[4];   // Z(n - 2)
+  T pend[4]; // s_y > 0: output row n - 2, computed one staged row earlier
 };
 
 __device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
@@ -232,85 +261,106 @@ __device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xf
 __device__ __forceinline__ double shfl_up1(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 __device__ __forceinline__ double shfl_dn1(double v) { return __shfl_down_sync(0xffffffffu, v, 1); }
 
-// One advection row for velocity k of quadrant (SX, SY).  `v` holds the newly
-// loaded row (a+1 if SY > 0, a+2 if SY < 0) at relative columns -4..7.  All 32
-// lanes of the warp must call it together (it exchanges neighbour columns).
-template <int SX, int SY, int ORDER, int LIM, typename T>
-__device__ __forceinline__ void advect_row(AdvState<T>& s, const T* v, const VelConst<T>& c,
+// One staged row n of velocity k in quadrant (SX, SY): `srow` points at the
+// thread's group start (own column 0) in the staged row, `out` receives the
+// advected row n - 2 (four values).  All 32 lanes of the warp must call it
+// together (it exchanges neighbour columns).
+template <int SX, int SY, int ORDER, int LIM, typename T, typename ST>
+__device__ __forceinline__ void advect_row(AdvState<T>& s, const ST* srow, const VelConst<T>& c,
                                            T* out) {
-  constexpr int B5 = SX > 0 ? -1 : 0;  // relative column of C5[0]
-  T Fn[5];
-#pragma unroll
-  for (int m = 0; m < 5; ++m) Fn[m] = v[4 + B5 + m];
+  // f of the staged row at columns -2..3 (SX > 0) or -1..4 (SX < 0): F[m] is
+  // column m - 2 resp. m - 1
+  T F[6];
+  if constexpr (SX > 0) {
+    sload<ST, T, 2>(srow - 2, F);
+    sload<ST, T, 4>(srow, F + 2);
+  } else {
+    sload<ST, T, 1>(srow - 1, F);
+    sload<ST, T, 4>(srow, F + 1);
+    sload<ST, T, 1>(srow + 4, F + 5);
+  }
+  constexpr int O = SX > 0 ? 2 : 1;  // index of own column 0 in F
 
-  T Bv[4], Bu = T(0), An[4];
+  // x direction: R^x(i) = f(i) - f(i-1), S^x(i) = half-limited R^x(i) with the
+  // upwind jump R^x(i - s_x); Z = f(i) - c_x (f(i) - f(i - s_x)) - ax dS^x(i)
+  T Z[4];
   if constexpr (ORDER == 2) {
-    T RYn[4], SYn[4];
+    T R[5];  // SX > 0: R^x(-1..3);  SX < 0: R^x(0..4)
+#pragma unroll
+    for (int m = 0; m < 5; ++m) R[m] = F[m + 1] - F[m];
+    T S[5];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int mo = i - B5;
-      if constexpr (SY > 0) {
-        RYn[i] = Fn[mo] - s.F0[mo];                   // R^y(a+1)
-        SYn[i] = half_limited<LIM>(RYn[i], s.RY[i]);  // S^y(a+1), upwind R^y(a)
-      } else {
-        RYn[i] = Fn[mo] - s.F1[mo];                   // R^y(a+2)
-        SYn[i] = half_limited<LIM>(s.RY[i], RYn[i]);  // S^y(a+1), upwind R^y(a+2)
-      }
-      Bv[i] = SYn[i] - s.SY[i];                       // S^y(a+1) - S^y(a)
-      s.RY[i] = RYn[i];
-      s.SY[i] = SYn[i];
+      if constexpr (SX > 0)
+        S[i] = half_limited<LIM>(R[i + 1], R[i]);
+      else
+        S[i] = half_limited<LIM>(R[i], R[i + 1]);
     }
-    // B one column upwind in x: the neighbouring group's edge column
-    if constexpr (SX > 0) Bu = shfl_up1(Bv[3]); else Bu = shfl_dn1(Bv[0]);
-    // x direction on the new row: R^x(c) = f(c) - f(c-1)
-    T RX[7];
+    S[4] = shfl_dn1(S[0]);  // S^x(4): the next group's column 0
 #pragma unroll
-    for (int j = 0; j < 7; ++j) RX[j] = v[3 + j] - v[2 + j];  // RX[j] = R^x(j-1)
-    T SXh[5];
+    for (int i = 0; i < 4; ++i) {
+      const T dS = S[i + 1] - S[i];
+      // f(i) - f(i - s_x) = s_x R^x(i) for s_x > 0, -R^x(i+1) for s_x < 0
+      const T X = SX > 0 ? fma(-c.cx, R[i + 1], F[O + i]) : fma(c.cx, R[i + 1], F[O + i]);
+      Z[i] = fma(-c.ax, dS, X);
+    }
+  } else {
 #pragma unroll
-    for (int m = 0; m < 4; ++m) SXh[m] = half_limited<LIM>(RX[m + 1], RX[m + 1 - SX]);
-    SXh[4] = shfl_dn1(SXh[0]);                         // column 4 = next group's column 0
-#pragma unroll
-    for (int i = 0; i < 4; ++i) An[i] = SXh[i + 1] - SXh[i];
+    for (int i = 0; i < 4; ++i) {
+      const T Rx = SX > 0 ? F[O + i] - F[O + i - 1] : F[O + i + 1] - F[O + i];
+      Z[i] = SX > 0 ? fma(-c.cx, Rx, F[O + i]) : fma(c.cx, Rx, F[O + i]);
+    }
   }
 
-  // output row a
+  // y direction and the output row
+  T o[4];
+  if constexpr (ORDER == 2) {
+    T Ry[4], Sy[4], dSy[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      Ry[i] = F[O + i] - s.Fp[i];  // R^y(n)
+      if constexpr (SY > 0) {
+        Sy[i] = half_limited<LIM>(Ry[i], s.Ryp[i]);  // S^y(n), upwind R^y(n - 1)
+      } else {
+        Sy[i] = half_limited<LIM>(s.Ryp[i], Ry[i]);  // S^y(n - 1), upwind R^y(n)
+      }
+      dSy[i] = Sy[i] - s.Syp[i];  // SY > 0: dS^y(n - 1);  SY < 0: dS^y(n - 2)
+    }
+    // dS^y one column upwind in x: the neighbouring group's edge column
+    const T du = SX > 0 ? shfl_up1(dSy[3]) : shfl_dn1(dSy[0]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const T dsu = SX > 0 ? (i > 0 ? dSy[i - 1] : du) : (i < 3 ? dSy[i + 1] : du);
+      // SY > 0: output row n - 1 from Z(n - 1), Z(n - 2); SY < 0: row n - 2
+      // from Z(n - 2), Z(n - 1)
+      const T Zi = SY > 0 ? s.Z1[i] : s.Z2[i];
+      const T Zu = SY > 0 ? s.Z2[i] : s.Z1[i];
+      T v = fma(c.cy, Zu - Zi, Zi);
+      v = fma(c.by0, dSy[i], v);
+      o[i] = fma(c.by1, dsu, v);
+      s.Ryp[i] = Ry[i];
+      s.Syp[i] = Sy[i];
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const T Zi = SY > 0 ? s.Z1[i] : s.Z2[i];
+      const T Zu = SY > 0 ? s.Z2[i] : s.Z1[i];
+      o[i] = fma(c.cy, Zu - Zi, Zi);
+    }
+  }
+
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int mo = i - B5;       // own column in C5
-    const int mu = i - SX - B5;  // x-upwind column in C5
-    T u1 = c.c00 * s.F0[mo] + c.c10 * s.F0[mu] + c.c01 * s.F1[mo] + c.c11 * s.F1[mu];
-    if constexpr (ORDER == 2) {
-      const int iu = i - SX;     // x-upwind column among the own four (or the neighbour's)
-      const T bu = (iu >= 0 && iu < 4) ? Bv[iu >= 0 && iu < 4 ? iu : 0] : Bu;
-      u1 -= c.a1 * s.A0[i] + c.a2 * s.A1[i];
-      u1 -= c.b1 * Bv[i] + c.b2 * bu;
-    }
-    out[i] = u1;
-  }
-
-  // shift the row history
-#pragma unroll
-  for (int m = 0; m < 5; ++m) {
     if constexpr (SY > 0) {
-      s.F1[m] = s.F0[m];
-      s.F0[m] = Fn[m];
+      out[i] = s.pend[i];
+      s.pend[i] = o[i];
     } else {
-      s.F0[m] = s.F1[m];
-      s.F1[m] = Fn[m];
+      out[i] = o[i];
     }
-  }
-  if constexpr (ORDER == 2) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      if constexpr (SY > 0) {
-        s.A1[i] = s.A0[i];
-        s.A0[i] = An[i];
-      } else {
-        s.A0[i] = s.A1[i];
-        s.A1[i] = An[i];
-      }
-    }
+    s.Fp[i] = F[O + i];
+    s.Z2[i] = s.Z1[i];
+    s.Z1[i] = Z[i];
   }
 }
 

@@ -14,11 +14,11 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// ------------------------------------------- TMA row loads and mbarriers
-// Interior strips stage whole rows with one tensor copy per row: a box of
-// SCOL columns x 1 row x 16 planes of f^n lands as [16][SCOL] in the ring slot,
-// the same layout the per-thread copies produce.  Completion is counted in
-// bytes on an mbarrier; every wait is bounded in time.
+// ------------------------------------- tensor copies, stores and mbarriers
+// A staged batch (RPI rows of SCOL columns x 16 planes) arrives by one tensor
+// copy into a ring slot laid out [RPI][16][SCOL]; completion is counted in
+// bytes on the slot's mbarrier, and every wait on it is bounded in time.  The
+// collision's output tile [RPI][16][TW] leaves by one tensor store.
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
 }
@@ -46,21 +46,21 @@ __device__ __forceinline__ unsigned long long global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Wait for the phase `parity` of `bar` to complete, for at most ~1 s; false on
-// timeout (the caller records the error and stops waiting).
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+// Wait for the phase `parity` of `bar` to complete, for at most `ns`
+// nanoseconds; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity,
+                                                  unsigned long long ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > 1000000000ULL) return false;
+    if (global_ns() - t0 > ns) return false;
   }
 }
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
-// One tensor copy of rows y.. of the (x, plane, row) tensor: the box's rows
-// land as consecutive [16][SCOL] ring slots.
+// One tensor copy of rows y.. of the (x, plane, row) tensor into `dst`.
 __device__ __forceinline__ void tma_load_rows(void* dst, const CUtensorMap* map, int x, int y,
                                               unsigned long long* bar) {
   asm volatile(
@@ -69,16 +69,39 @@ __device__ __forceinline__ void tma_load_rows(void* dst, const CUtensorMap* map,
       "l"(map), "r"(x), "r"(0), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+// One tensor store of the tile at `src` to rows y.. of the (x, plane, row) tensor.
+__device__ __forceinline__ void tma_store_rows(const CUtensorMap* map, int x, int y,
+                                               const void* src) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(
+          map),
+      "r"(x), "r"(0), "r"(y), "r"(smem_u32(src))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+// at most N committed store groups may still be reading shared memory
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(N) : "memory");
+}
+// every committed store group has completed (its writes are performed)
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+}
 
 __device__ __forceinline__ int mod_pos(int a, int n) {  // a mod n for a > -n*1024
   return (a + n * 1024) % n;
 }
 
-// Shared-memory layout: the staging ring in the storage type ST, the rings of
-// advected rows and moments in the arithmetic type T, then ints.
+// Shared-memory layout: the staging ring and the output tiles in the storage
+// type ST, the rings of advected rows and moments in the arithmetic type T,
+// then ints.  All moment rings are indexed by lattice row mod MROWS.
 template <typename T, typename ST>
 struct Smem {
-  ST* stage;  // [SROWS][16][SCOL] f^n rows of the strip, one group of halo per side
+  ST* stage;  // [2][RPI][16][SCOL] f^n rows of the strip, one group of halo per side
+  ST* out;    // [2][RPI][16][TW] f^{n+1} tiles for the tensor store
   T* fs;      // [FROWS][16][REG] advected f*
   T* rho;     // [MROWS][REG]
   T* drho;    // rho* - rho_ref
@@ -88,13 +111,14 @@ struct Smem {
   T* lap;     // 9-point Laplacian of rho*
   int* col;   // [SG] wrapped global column of each staging group
   unsigned long long* dsums;  // [6] fused diagnostics: per-CTA bubble-site sums
-  unsigned long long* bar;    // [2] mbarriers of the tensor-copy batches (even, odd)
+  unsigned long long* bar;    // [2] mbarriers of the staging slots
   int* abort;                 // a bounded wait of this CTA timed out: stop waiting
   __device__ Smem(unsigned char* raw) {
-    // the ring starts on 128 bytes (tensor copies); the allocation has the slack
+    // tensor copies need 128-byte aligned tiles; the allocation has the slack
     raw += (128u - ((unsigned)__cvta_generic_to_shared(raw) & 127u)) & 127u;
     stage = reinterpret_cast<ST*>(raw);
-    T* p = reinterpret_cast<T*>(raw + sizeof(ST) * SROWS * 16 * SCOL);
+    out = stage + SROWS * 16 * SCOL;
+    T* p = reinterpret_cast<T*>(out + 2 * RPI * 16 * TW);
     fs = p;
     p += FROWS * 16 * REG;
     rho = p;
@@ -110,9 +134,10 @@ struct Smem {
   }
 };
 
-// Staging: a staged row holds 16 planes x CH 16-byte chunks.  Thread t copies
-// chunks t, t + NT, ... of every staged row, so its (plane, column) slots are
-// fixed for a whole segment and a row costs one address add per chunk.
+// Per-thread copies of staged rows (strips at the periodic x seam, lattices
+// without tensor maps): a staged row holds 16 planes x CH 16-byte chunks;
+// thread t copies chunks t, t + NT, ..., so its (plane, column) slots are
+// fixed for a whole segment.
 template <typename T, typename ST>
 struct StageSlots {
   static constexpr int CH = SCOL * (int)sizeof(ST) / 16;  // 16-byte chunks per plane row
@@ -133,154 +158,131 @@ struct StageSlots {
   }
 };
 
-// Stage rows [r_begin, r_end) of f^n for all 16 planes into the staging ring
-// (asynchronously when VEC).  Rows outside the lattice are wall ghost rows
-// (constant per plane) or wrap periodically.
-template <typename T, typename ST, bool VEC>
-__device__ __forceinline__ void stage_rows(const StepArgs<T>& P, const Smem<T, ST>& S,
-                                           const StageSlots<T, ST>& sl, int r_begin, int r_end,
-                                           int rbase) {
+// Wall ghost row (constant per plane) into a staged row.
+template <typename T, typename ST>
+__device__ __forceinline__ void stage_ghost_row(const StepArgs<T>& P, const StageSlots<T, ST>& sl,
+                                                ST* srow, bool bottom) {
   using SS = StageSlots<T, ST>;
-  for (int r = r_begin; r < r_end; ++r) {
-    ST* srow = S.stage + mod_pos(r - rbase, SROWS) * 16 * SCOL;
-    if (P.walls && (r < 0 || r >= P.Ly)) {
 #pragma unroll
-      for (int m = 0; m < SS::NS; ++m) {
-        const int c = threadIdx.x + NT * m;
-        if (c < SS::PER_ROW) {
-          const int k = c / SS::CH;
-          const ST gv = to_store<ST, T>(r < 0 ? P.v[k].gbot : P.v[k].gtop);
+  for (int m = 0; m < SS::NS; ++m) {
+    const int c = threadIdx.x + NT * m;
+    if (c < SS::PER_ROW) {
+      const int k = c / SS::CH;
+      const ST gv = to_store<ST, T>(bottom ? P.v[k].gbot : P.v[k].gtop);
 #pragma unroll
-          for (int e = 0; e < SS::EPC; ++e) srow[sl.dst[m] + e] = gv;
-        }
-      }
-      continue;
-    }
-    const int rw = r < 0 ? r + P.Ly * ((-r + P.Ly - 1) / P.Ly) : (r >= P.Ly ? r % P.Ly : r);
-    const ST* frow = static_cast<const ST*>(P.fin) + (long long)rw * P.Lx;
-#pragma unroll
-    for (int m = 0; m < SS::NS; ++m) {
-      const int c = threadIdx.x + NT * m;
-      if (c < SS::PER_ROW) {
-        if (VEC) {
-          cp_async16(srow + sl.dst[m], frow + sl.src[m]);
-        } else {
-          const int k = c / SS::CH, ch = c - k * SS::CH;
-          const ST* fk = frow + (long long)k * P.plane;
-          const int x0 = S.col[0];  // unwrapped first staging column (scalar path)
-#pragma unroll
-          for (int e = 0; e < SS::EPC; ++e)
-            srow[sl.dst[m] + e] = __ldg(fk + wrapi(x0 + ch * SS::EPC + e, P.Lx));
-        }
-      }
+      for (int e = 0; e < SS::EPC; ++e) srow[sl.dst[m] + e] = gv;
     }
   }
 }
 
-// Tensor-copy staging of rows [r_begin, r_end) for a strip whose staging
-// columns [x0, x0 + SCOL) lie inside the lattice.  Ring slot of row r:
-// (r - rbase) mod SROWS, so every batch of RPI rows starting at rbase + RPI i
-// fills RPI consecutive slots and, away from the lattice's y ends, is ONE copy
-// through the RPI-row map; rows that wrap periodically or sit next to a wall go
-// one per copy through the 1-row map.  Thread 0 arms the batch's mbarrier with
-// the byte count first; wall ghost rows (constant per plane) are written by
-// all threads.  `fence` orders earlier generic writes of the ring (ghost rows)
-// before the copies.
-template <typename T, typename ST>
-__device__ __forceinline__ void stage_rows_tma(const StepArgs<T>& P, const Smem<T, ST>& S,
-                                               const StageSlots<T, ST>& sl, const CUtensorMap* tm,
-                                               int x0, int r_begin, int r_end, int rbase,
-                                               unsigned batch, bool fence) {
+// Issue staged batch `g` (rows r0 .. r0+RPI-1) into ring slot g & 1: one
+// tensor copy (TMA, thread 0) when the batch lies inside the lattice, else
+// one copy per row (periodic wrap in y) and ghost rows written by all threads
+// (walls); per-thread cp.async copies (VEC) or plain loads when the strip
+// cannot use the tensor map.  Every batch arrives once on the slot's mbarrier
+// (with the tensor copies' byte count, zero otherwise), so the barrier's phase
+// parity is (g >> 1) & 1 for every batch.
+template <typename T, typename ST, bool VEC>
+__device__ __forceinline__ void issue_batch(const StepArgs<T>& P, const Smem<T, ST>& S,
+                                            const StageSlots<T, ST>& sl, const CUtensorMap* tm,
+                                            bool tma, int x0, int r0, unsigned g, unsigned& gi) {
   using SS = StageSlots<T, ST>;
   constexpr unsigned ROW_BYTES = 16u * SCOL * (unsigned)sizeof(ST);
   const int Ly = P.Ly;
-  if (threadIdx.x == 0) {
-    unsigned long long* bar = S.bar + (batch & 1u);
-    if (fence) fence_proxy_async();
-    if (r_end - r_begin == RPI && r_begin >= 0 && r_end <= Ly &&
-        mod_pos(r_begin - rbase, RPI) == 0) {
-      mbar_arrive_expect_tx(bar, RPI * ROW_BYTES);
-      tma_load_rows(S.stage + mod_pos(r_begin - rbase, SROWS) * 16 * SCOL, tm, x0, r_begin, bar);
-    } else {
-      unsigned bytes = 0;
-      for (int r = r_begin; r < r_end; ++r)
-        if (!(P.walls && (r < 0 || r >= Ly))) bytes += ROW_BYTES;
-      mbar_arrive_expect_tx(bar, bytes);
-      for (int r = r_begin; r < r_end;) {
-        ST* dst = S.stage + mod_pos(r - rbase, SROWS) * 16 * SCOL;
-        if (mod_pos(r - rbase, RPI) == 0 && r + RPI <= r_end && r >= 0 && r + RPI <= Ly) {
-          tma_load_rows(dst, tm, x0, r, bar);  // an aligned batch inside the lattice
-          r += RPI;
-          continue;
+  ST* base = S.stage + (g & 1u) * (RPI * 16 * SCOL);
+  unsigned long long* bar = S.bar + (g & 1u);
+  const bool touches_wall = P.walls && (r0 < 0 || r0 + RPI > Ly);
+  if (touches_wall) {
+    for (int r = 0; r < RPI; ++r) {
+      const int row = r0 + r;
+      if (row < 0 || row >= Ly) stage_ghost_row<T, ST>(P, sl, base + r * 16 * SCOL, row < 0);
+    }
+    // these generic writes precede later tensor copies into the same slot
+    fence_proxy_async();
+  }
+  // after a timed-out wait thread 0 arms and issues nothing more: no copy can
+  // then be in flight except the batches armed before (drain_copies waits for them)
+  const bool arm = threadIdx.x == 0 && !*reinterpret_cast<volatile int*>(S.abort);
+  if (arm) gi = g + 1u;
+  if (tma) {
+    if (arm) {
+      if (r0 >= 0 && r0 + RPI <= Ly) {
+        mbar_arrive_expect_tx(bar, RPI * ROW_BYTES);
+        tma_load_rows(base, tm, x0, r0, bar);
+      } else {
+        unsigned bytes = 0;
+        for (int r = 0; r < RPI; ++r)
+          if (!(P.walls && (r0 + r < 0 || r0 + r >= Ly))) bytes += ROW_BYTES;
+        mbar_arrive_expect_tx(bar, bytes);
+        for (int r = 0; r < RPI; ++r) {
+          const int row = r0 + r;
+          if (P.walls && (row < 0 || row >= Ly)) continue;
+          tma_load_rows(base + r * 16 * SCOL, tm + 1, x0, wrapi(row, Ly), bar);
         }
-        if (!(P.walls && (r < 0 || r >= Ly))) {
-          int rw = r % Ly;
-          if (rw < 0) rw += Ly;
-          tma_load_rows(dst, tm + 1, x0, rw, bar);
-        }
-        ++r;
       }
     }
-  }
-  if (P.walls && (r_begin < 0 || r_end > Ly)) {
-    for (int r = r_begin; r < r_end; ++r) {
-      if (r >= 0 && r < Ly) continue;
-      ST* srow = S.stage + mod_pos(r - rbase, SROWS) * 16 * SCOL;
+  } else {
+    for (int r = 0; r < RPI; ++r) {
+      const int row = r0 + r;
+      if (P.walls && (row < 0 || row >= Ly)) continue;
+      ST* srow = base + r * 16 * SCOL;
+      const ST* frow = static_cast<const ST*>(P.fin) + (long long)wrapi(row, Ly) * P.Lx;
 #pragma unroll
       for (int m = 0; m < SS::NS; ++m) {
         const int c = threadIdx.x + NT * m;
         if (c < SS::PER_ROW) {
-          const ST gv = to_store<ST, T>(r < 0 ? P.v[c / SS::CH].gbot : P.v[c / SS::CH].gtop);
+          if (VEC) {
+            cp_async16(srow + sl.dst[m], frow + sl.src[m]);
+          } else {
+            const int k = c / SS::CH, ch = c - k * SS::CH;
+            const ST* fk = frow + (long long)k * P.plane;
+            const int xs = S.col[0];  // unwrapped first staging column (scalar path)
 #pragma unroll
-          for (int e = 0; e < SS::EPC; ++e) srow[sl.dst[m] + e] = gv;
+            for (int e = 0; e < SS::EPC; ++e)
+              srow[sl.dst[m] + e] = __ldg(fk + wrapi(xs + ch * SS::EPC + e, P.Lx));
+          }
         }
       }
     }
+    if (arm) mbar_arrive_expect_tx(bar, 0u);
   }
+  cp_async_commit();
 }
 
-// Every thread waits for tensor-copy batch `batch` (bounded); a timeout sets
-// the step's error bit 2 and the CTA stops waiting (its results are void).
+// Every thread waits for staged batch g (bounded); per-thread copies also need
+// the CTA barrier that makes the other threads' copies visible.  A timeout
+// sets error bit 1 and records the batch (abort = g + 1): the CTA stops
+// waiting and issuing, its results are void.
 template <typename T, typename SM>
-__device__ __forceinline__ void tma_wait_batch(const StepArgs<T>& P, const SM& S, unsigned batch) {
-  if (*reinterpret_cast<volatile int*>(S.abort)) return;
-  if (!mbar_wait_bounded(S.bar + (batch & 1u), (batch >> 1) & 1u)) {
-    *reinterpret_cast<volatile int*>(S.abort) = 1;
-    atomicOr(P.err, 2u);
+__device__ __forceinline__ void wait_batch(const StepArgs<T>& P, const SM& S, unsigned g,
+                                           bool tma) {
+  if (!*reinterpret_cast<volatile int*>(S.abort)) {
+    if (!mbar_wait_bounded(S.bar + (g & 1u), (g >> 1) & 1u, 1000000000ULL)) {
+      *reinterpret_cast<volatile int*>(S.abort) = (int)(g + 1u);
+      atomicOr(P.err, 2u);
+    }
+  }
+  if (!tma) {
+    cp_async_wait<1>();
+    __syncthreads();
   }
 }
 
-// P1 for one warp quadrant: rows a0 .. a0+RPI-1 of plane k, two rows per loop
-// trip so that the two-row history rotates by register renaming.
+// P1 for one warp quadrant: the RPI staged rows of the batch in slot `sbase`,
+// advected rows to the f* ring at `fbase` (thread's plane and group).
 template <int SX, int SY, int ORDER, int LIM, typename T, typename ST>
-__device__ __forceinline__ void advect_rows(const StepArgs<T>& P, const Smem<T, ST>& S,
-                                            AdvState<T>& st, const VelConst<T>& vc, int a0,
-                                            int rbase, int src_off, int dst_off, bool ghosts) {
-  constexpr int LAG = SY > 0 ? 1 : 2;  // staged row read for output row a
-  int slot = mod_pos(a0 + LAG - rbase, SROWS);
-#pragma unroll 1
-  for (int j = 0; j < RPI; j += 2) {
+__device__ __forceinline__ void advect_batch(AdvState<T>& st, const VelConst<T>& vc,
+                                             const ST* sbase, T* fbase) {
 #pragma unroll
-    for (int jj = 0; jj < 2; ++jj) {
-      const int a = a0 + j + jj;
-      T v[12];
-      const ST* srow = S.stage + slot * (16 * SCOL) + src_off;
-      slot = slot == SROWS - 1 ? 0 : slot + 1;
-      sload12(srow, v);
-      T out[4];
-      advect_row<SX, SY, ORDER, LIM>(st, v, vc, out);
-      if (ghosts && (a < 0 || a >= P.Ly)) {  // ghost rows keep f^eq(rho_ext, u_wall)
-        const T gv = a < 0 ? vc.gbot : vc.gtop;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) out[i] = gv;
-      }
-      T* dst = S.fs + (a & (FROWS - 1)) * (16 * REG) + dst_off;
-      if constexpr (sizeof(T) == 4) {
-        *reinterpret_cast<float4*>(dst) = make_float4(out[0], out[1], out[2], out[3]);
-      } else {
-        reinterpret_cast<double2*>(dst)[0] = make_double2(out[0], out[1]);
-        reinterpret_cast<double2*>(dst)[1] = make_double2(out[2], out[3]);
-      }
+  for (int r = 0; r < RPI; ++r) {
+    T out[4];
+    advect_row<SX, SY, ORDER, LIM>(st, sbase + r * (16 * SCOL), vc, out);
+    T* dst = fbase + r * (16 * REG);
+    if constexpr (sizeof(T) == 4) {
+      *reinterpret_cast<float4*>(dst) = make_float4(out[0], out[1], out[2], out[3]);
+    } else {
+      reinterpret_cast<double2*>(dst)[0] = make_double2(out[0], out[1]);
+      reinterpret_cast<double2*>(dst)[1] = make_double2(out[2], out[3]);
     }
   }
 }
@@ -288,297 +290,338 @@ __device__ __forceinline__ void advect_rows(const StepArgs<T>& P, const Smem<T, 
 // One row segment [ys, ye) of one strip of one lattice.  Every node's update
 // uses the same arithmetic in the same order whatever the segment boundaries,
 // so results do not depend on how the rows are split over CTAs or lattices.
+//
+// Iteration i consumes staged batch B_i = ys - 4 + 4 i .. +3 and, in the same
+// iteration, P1 writes f* of rows B_i - 2 .., P2 their moments, P3 the
+// Laplacian of rows B_i - 3 .., P4 the outputs of rows B_i - 4 .. = ys + 4 (i -
+// WARM) ..  (rings indexed by (row - ys + 6) mod 8).  The tile of P4(i) leaves
+// by a tensor store issued by thread 0 at the start of iteration i + 1 (or
+// after the loop), after the barrier that ends P4(i).
 template <typename T, typename ST, int ORDER, int LIM, bool VEC, bool DIAG>
 __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, ST>& S, int strip,
-                                            int ys, int ye, const CUtensorMap* tm,
-                                            unsigned& batch, double& dmass) {
+                                            int ys, int ye, const CUtensorMap* tm, unsigned& gb,
+                                            unsigned& gi, double& dmass) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   // P1 layout: a warp = one sign quadrant x two velocity groups x 16 column
   // groups, so column neighbours are adjacent lanes
-  const int q = warp & 3;                               // sign quadrant of the warp
-  const int g = lane & 15;                              // column group 0..15
+  const int q = warp & 3;                                       // sign quadrant of the warp
+  const int g = lane & 15;                                      // column group 0..15
   const int k = ((((warp >> 2) << 1) | (lane >> 4)) << 2) | q;  // velocity of this thread
   const VelConst<T> vc = P.v[k];
   const int Lx = P.Lx, Ly = P.Ly;
-  {
 
-    // wrapped global columns of the staging groups (region column 0 is global
-    // column strip*TW - XOFF; the first staging column is region column -4)
-    __syncthreads();  // previous segment done with S.col and the rings
-    if (tid < SG) {
-      const int x = strip * TW - XOFF - 4 + 4 * tid;
-      S.col[tid] = VEC ? wrapi(x, Lx) : (tid == 0 ? x : 0);
+  // wrapped global columns of the staging groups (region column 0 is global
+  // column strip*TW - XOFF; the first staging column is region column -4)
+  __syncthreads();  // previous segment done with S.col and the rings
+  if (tid < SG) {
+    const int x = strip * TW - XOFF - 4 + 4 * tid;
+    S.col[tid] = VEC ? wrapi(x, Lx) : (tid == 0 ? x : 0);
+  }
+  __syncthreads();
+
+  AdvState<T> st;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    st.Fp[i] = st.Ryp[i] = st.Syp[i] = st.Z1[i] = st.Z2[i] = st.pend[i] = T(0);
+
+  const StageSlots<T, ST> slots(P, S, VEC);
+  // interior strips stage by tensor copies, the strips at the periodic x
+  // seam (and lattices without a tensor map) by per-thread copies
+  const int x0 = strip * TW - XOFF - 4;
+  const bool tma = VEC && P.tma_in && x0 >= 0 && x0 + SCOL <= Lx;
+  const bool tstore = VEC && P.tma_out;
+  const int nit = WARM + (ye - ys + RPI - 1) / RPI;
+  const unsigned g0 = gb;
+
+  // per-thread bases: P1 (plane k, group g), P2 (node row r2, column c2),
+  // P3 (row r3, column c3), P4 (row r4, output column)
+  const ST* p1_src = S.stage + k * SCOL + 4 * g + 4;
+  T* p1_dst = S.fs + k * REG + 4 * g;
+  const int r2 = tid >> 6, c2 = tid & 63;
+  const bool p3_on = tid < RPI * (REG - 2);
+  const int r3 = tid / (REG - 2), c3 = 1 + tid - r3 * (REG - 2);
+  const bool p4_on = tid < P4T;
+  const int r4 = tid / TW, o4 = tid - r4 * TW;  // output column o4 of the strip
+  const int c4 = XOFF + o4, x4 = strip * TW + o4;
+
+  issue_batch<T, ST, VEC>(P, S, slots, tm, tma, x0, ys - 4, g0, gi);
+
+  T dseg = T(0);  // fused diagnostics: mass of this thread's nodes (rho - rho_ref)
+  int nseg = 0;
+  for (int it = 0; it < nit; ++it) {
+    const unsigned gcur = g0 + (unsigned)it;
+    const int B = ys - 4 + RPI * it;  // first staged row of this iteration
+    // ---------------- L: next batch, the previous iteration's output tile
+    if (it + 1 < nit) issue_batch<T, ST, VEC>(P, S, slots, tm, tma, x0, B + RPI, gcur + 1, gi);
+    else cp_async_commit();
+    if (tstore && tid == 0) {
+      bool stored = false;
+      if (it - 1 >= WARM) {
+        const int row0 = ys + RPI * (it - 1 - WARM);
+        const ST* tile = S.out + ((it - 1) & 1) * (RPI * 16 * TW);
+        if (row0 + RPI <= ye) {
+          tma_store_rows(tm + 2, strip * TW, row0, tile);
+        } else {
+          for (int r = 0; row0 + r < ye; ++r)
+            tma_store_rows(tm + 3, strip * TW, row0 + r, tile + r * 16 * TW);
+        }
+        bulk_commit();
+        stored = true;
+      }
+      // the tile P4 writes next was last stored two iterations ago
+      if (stored) bulk_wait_read<1>(); else bulk_wait_read<0>();
+    }
+    wait_batch(P, S, gcur, tma);
+
+    // ---------------- P1: advect the staged batch into f* rows B - 2 ..
+    {
+      const ST* sb = p1_src + (gcur & 1u) * (RPI * 16 * SCOL);
+      T* fb = p1_dst + (it & 1) * (RPI * 16 * REG);
+      switch (q) {
+        case 0: advect_batch<+1, +1, ORDER, LIM>(st, vc, sb, fb); break;
+        case 1: advect_batch<-1, +1, ORDER, LIM>(st, vc, sb, fb); break;
+        case 2: advect_batch<-1, -1, ORDER, LIM>(st, vc, sb, fb); break;
+        default: advect_batch<+1, -1, ORDER, LIM>(st, vc, sb, fb); break;
+      }
+      // wall ghost rows keep f^eq(rho_ext, u_wall)
+      if (P.walls && (B - 2 < 0 || B + 2 > Ly)) {
+#pragma unroll
+        for (int r = 0; r < RPI; ++r) {
+          const int a = B - 2 + r;
+          if (a < 0 || a >= Ly) {
+            const T gv = a < 0 ? vc.gbot : vc.gtop;
+            T* dst = fb + r * (16 * REG);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) dst[m] = gv;
+          }
+        }
+      }
     }
     __syncthreads();
 
-    AdvState<T> st;
+    // ---------------- P2: moments of rows B - 2 .., one thread per node
+    if (it >= 1) {
+      const int sl = (it & 1) * RPI + r2;
+      const T* src = S.fs + sl * (16 * REG) + c2;
+      T f[16];
 #pragma unroll
-    for (int m = 0; m < 5; ++m) st.F0[m] = st.F1[m] = T(0);
+      for (int kk = 0; kk < 16; ++kk) f[kk] = src[kk * REG];
+      // velocity order: k = 4*group + sign, groups (lo,lo),(hi,lo),(lo,hi),(hi,hi),
+      // signs (+,+),(-,+),(-,-),(+,-): per group A = f(++) - f(--), B = f(-+) - f(+-)
+      T d[4], sx[4], sy[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) st.RY[i] = st.SY[i] = st.A0[i] = st.A1[i] = T(0);
-
-    // P4 thread -> node mapping: a warp pair per row, 32 + 24 output columns
-    const int p4_row = warp >> 1;                           // 0..3 within the iteration
-    const int p4_col = XOFF + 32 * (warp & 1) + lane;       // region column
-    const int p4_x = strip * TW + p4_col - XOFF;            // global output column
-    const bool p4_col_ok = p4_col < XOFF + TW && p4_x < Lx;
-
-    const StageSlots<T, ST> slots(P, S, VEC);
-    // interior strips stage by tensor copies, the strips at the periodic x
-    // seam (and lattices without a tensor map) by per-thread copies
-    const int x0 = strip * TW - XOFF - 4;
-    const bool tma = VEC && tm != nullptr && x0 >= 0 && x0 + SCOL <= Lx;
-    // ghost rows are written by threads into slots the copies reuse later
-    const bool fence = P.walls && (ys < 2 * SROWS || ye + 2 * SROWS > Ly);
-    int a0 = ys - WARMUP;
-    const int rbase = a0 + 2;  // first row of every iteration's batch: rbase + RPI i
-    if (tma)
-      stage_rows_tma<T, ST>(P, S, slots, tm, x0, a0 + 1, a0 + RPI + 2, rbase, batch, fence);
-    else
-      stage_rows<T, ST, VEC>(P, S, slots, a0 + 1, a0 + RPI + 2, rbase);
-    cp_async_commit();
-
-    // fused diagnostics: this thread's mass over the segment, as the sum of
-    // rho - rho_ref (small in the liquid, so FP32 keeps it exact to ~1e-7 of
-    // the node count) plus rho_ref times its node count
-    T dseg = T(0);
-    int nseg = 0;
-    for (; a0 - 2 < ye; a0 += RPI) {
-      // ---------------- L: prefetch the rows only the next iteration needs
-      const bool more = (a0 + RPI) - 2 < ye;
-      if (tma) {
-        if (more)
-          stage_rows_tma<T, ST>(P, S, slots, tm, x0, a0 + RPI + 2, a0 + 2 * RPI + 2, rbase,
-                                batch + 1, fence);
-        tma_wait_batch(P, S, batch);
-        ++batch;
-      } else {
-        if (more) stage_rows<T, ST, VEC>(P, S, slots, a0 + RPI + 2, a0 + 2 * RPI + 2, rbase);
-        cp_async_commit();
-        cp_async_wait<1>();
+      for (int gg = 0; gg < 4; ++gg) {
+        const T* fg = f + 4 * gg;
+        const T A = fg[0] - fg[2], Bm = fg[1] - fg[3];
+        sx[gg] = A - Bm;
+        sy[gg] = A + Bm;
+        d[gg] = (fg[0] + fg[2]) + (fg[1] + fg[3]);
       }
-      __syncthreads();
+      const T dr = (d[0] + d[1]) + (d[2] + d[3]);
+      const T mx = P.xlo * (sx[0] + sx[2]) + P.xhi * (sx[1] + sx[3]);
+      const T my = P.xlo * (sy[0] + sy[1]) + P.xhi * (sy[2] + sy[3]);
+      const T rho = P.rho_ref + dr;
+      const T ir = rcp(rho);
+      const int m = sl * REG + c2;
+      S.rho[m] = rho;
+      S.drho[m] = dr;
+      S.ux[m] = mx * ir;
+      S.uy[m] = my * ir;
+      // p^i - p^w = rho T - [rho T/(1 - b rho) - a rho^2]   (Eqs. eder, evdw)
+      const T rT = rho * P.Tt;
+      S.phi[m] = fma(P.a * rho, rho, rT - rT * rcp(T(1) - P.b * rho));
+    }
+    __syncthreads();
 
-      // ---------------- P1: advect rows a0 .. a0+RPI-1 of plane k
-      {
-        const bool ghosts = P.walls && (a0 < 0 || a0 + RPI > Ly);  // any wall ghost row here
-        const int so = k * SCOL + 4 * g, dof = k * REG + 4 * g;
-        switch (q) {
-          case 0: advect_rows<+1, +1, ORDER, LIM>(P, S, st, vc, a0, rbase, so, dof, ghosts); break;
-          case 1: advect_rows<-1, +1, ORDER, LIM>(P, S, st, vc, a0, rbase, so, dof, ghosts); break;
-          case 2: advect_rows<-1, -1, ORDER, LIM>(P, S, st, vc, a0, rbase, so, dof, ghosts); break;
-          default: advect_rows<+1, -1, ORDER, LIM>(P, S, st, vc, a0, rbase, so, dof, ghosts); break;
-        }
-      }
-      __syncthreads();
+    // ---------------- P3: Laplacian of rho* on rows B - 3 ..
+    if (it >= 1 && p3_on) {
+      const int s0 = ((it & 1) * RPI + r3 + 7) & 7;  // row B - 3 + r3
+      const T* R0 = S.rho + s0 * REG + c3;
+      const T* Rm = S.rho + ((s0 + 7) & 7) * REG + c3;
+      const T* Rp = S.rho + ((s0 + 1) & 7) * REG + c3;
+      const T nn = (R0[-1] + R0[1]) + (Rm[0] + Rp[0]);
+      const T dg = (Rm[-1] + Rm[1]) + (Rp[-1] + Rp[1]);
+      S.lap[s0 * REG + c3] = fma(P.lp1, nn, fma(P.lp2, dg, -P.lp0 * R0[0]));
+    }
+    __syncthreads();
 
-      // ---------------- P2: moments of rows a0 .. a0+3, one thread per node
-      {
-        const int r = a0 + (tid >> 6), col = tid & 63;
-        const T* src = S.fs + (r & (FROWS - 1)) * 16 * REG + col;
+    // ---------------- P4: g, collision of all planes, output tile (rows B - 4 ..)
+    if (it >= WARM && p4_on) {
+      const int c = B - 4 + r4;  // lattice row
+      T rho_post = T(-1);        // post-step density of this thread's node, if it has one
+      if (c < ye && x4 < Lx) {
+        const int s0 = ((it & 1) * RPI + r4 + 6) & 7;
+        const int sc = s0 * REG + c4;
+        const int sm = ((s0 + 7) & 7) * REG + c4;
+        const int sp = ((s0 + 1) & 7) * REG + c4;
+        const int s2m = ((s0 + 6) & 7) * REG + c4;
+        const int s2p = ((s0 + 2) & 7) * REG + c4;
+        const T* ph = S.phi;
+        const T* lp = S.lap;
+        // fourth-order 5x5 gradient of p^i - p^w: the combination (4 D_h - D_2h)/3
+        // of the isotropic 3x3 gradient D_h at spacings ds and 2 ds (times dt/ds)
+        const T px = P.gw1 * (ph[sc + 1] - ph[sc - 1]) +
+                     P.gw2 * ((ph[sp + 1] - ph[sp - 1]) + (ph[sm + 1] - ph[sm - 1])) -
+                     P.gw3 * (ph[sc + 2] - ph[sc - 2]) -
+                     P.gw4 * ((ph[s2p + 2] - ph[s2p - 2]) + (ph[s2m + 2] - ph[s2m - 2]));
+        const T py = P.gw1 * (ph[sp] - ph[sm]) +
+                     P.gw2 * ((ph[sp + 1] - ph[sm + 1]) + (ph[sp - 1] - ph[sm - 1])) -
+                     P.gw3 * (ph[s2p] - ph[s2m]) -
+                     P.gw4 * ((ph[s2p + 2] - ph[s2m + 2]) + (ph[s2p - 2] - ph[s2m - 2]));
+        // isotropic 3x3 gradient of the Laplacian (times kappa dt/ds)
+        const T lx = P.lw1 * (lp[sc + 1] - lp[sc - 1]) +
+                     P.lw2 * ((lp[sp + 1] - lp[sp - 1]) + (lp[sm + 1] - lp[sm - 1]));
+        const T ly = P.lw1 * (lp[sp] - lp[sm]) +
+                     P.lw2 * ((lp[sp + 1] - lp[sm + 1]) + (lp[sp - 1] - lp[sm - 1]));
+        const T rho = S.rho[sc], ux = S.ux[sc], uy = S.uy[sc], drho = S.drho[sc];
+        const T ir = rcp(rho);
+        const T gdx = fma(ir, px, lx);  // dt xi.g components: dt g
+        const T gdy = fma(ir, py, ly);
+        if (!(rho > T(0)) || !(rho < T(1e30))) atomicOr(P.err, 1u);
+        const T e = T(1) - T(0.5) * (ux * ux + uy * uy);
+        const T h = gdx * ux + gdy * uy;
+        const T p0 = P.omega * drho * ir + P.omega * (e - T(1)) - h;
+        const T p1 = e - P.Tt + T(1);
+        const T p2 = P.omega * e - h;
+        const T lo = P.xlo, hi = P.xhi;
+        const T mxu[2] = {lo * ux, hi * ux}, myu[2] = {lo * uy, hi * uy};
+        const T mxg[2] = {lo * gdx, hi * gdx}, myg[2] = {lo * gdy, hi * gdy};
+
         T f[16];
+        const T* src = S.fs + s0 * (16 * REG) + c4;
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) f[kk] = src[kk * REG];
-        // velocity order: k = 4*group + sign, groups (lo,lo),(hi,lo),(lo,hi),(hi,hi),
-        // signs (+,+),(-,+),(-,-),(+,-)
-        T d = T(0);
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) d += f[kk];
-        const T sxa = (f[0] - f[1] - f[2] + f[3]) + (f[8] - f[9] - f[10] + f[11]);
-        const T sxb = (f[4] - f[5] - f[6] + f[7]) + (f[12] - f[13] - f[14] + f[15]);
-        const T sya = (f[0] + f[1] - f[2] - f[3]) + (f[4] + f[5] - f[6] - f[7]);
-        const T syb = (f[8] + f[9] - f[10] - f[11]) + (f[12] + f[13] - f[14] - f[15]);
-        const T mx = P.xlo * sxa + P.xhi * sxb;
-        const T my = P.xlo * sya + P.xhi * syb;
-        const T rho = P.rho_ref + d;
-        const T ir = rcp(rho);
-        const int sl = (r & (MROWS - 1)) * REG + col;
-        S.rho[sl] = rho;
-        S.drho[sl] = d;
-        S.ux[sl] = mx * ir;
-        S.uy[sl] = my * ir;
-        // p^i - p^w = rho T - [rho T/(1 - b rho) - a rho^2]   (Eqs. eder, evdw)
-        const T rT = rho * P.Tt;
-        S.phi[sl] = rT - rT * rcp(T(1) - P.b * rho) + P.a * rho * rho;
-      }
-      __syncthreads();
 
-      // ---------------- P3: Laplacian of rho* on rows a0-1 .. a0+2
-      if (tid < (REG - 2) * RPI) {
-        const int rr = tid / (REG - 2);
-        const int col = 1 + tid - rr * (REG - 2), r = a0 - 1 + rr;
-        const T* R0 = S.rho + (r & (MROWS - 1)) * REG + col;
-        const T* Rm = S.rho + ((r - 1) & (MROWS - 1)) * REG + col;
-        const T* Rp = S.rho + ((r + 1) & (MROWS - 1)) * REG + col;
-        const T nn = R0[-1] + R0[1] + Rm[0] + Rp[0];
-        const T dg = Rm[-1] + Rm[1] + Rp[-1] + Rp[1];
-        S.lap[(r & (MROWS - 1)) * REG + col] =
-            (T(2) / T(3) * nn + dg / T(6) - T(10) / T(3) * R0[0]) * P.inv_ds2;
-      }
-      __syncthreads();
-
-      // ---------------- P4: g, collision of all planes, store (rows a0-2 .. a0+1)
-      {
-        const int c = a0 - 2 + p4_row;
-        T rho_post = T(-1);  // post-step density of this thread's node, if it has one
-        if (p4_col_ok && c >= ys && c < ye) {
-          const int col = p4_col;
-          const int sc = (c & (MROWS - 1)) * REG + col;
-          const int sm = ((c - 1) & (MROWS - 1)) * REG + col;
-          const int sp = ((c + 1) & (MROWS - 1)) * REG + col;
-          const int s2m = ((c - 2) & (MROWS - 1)) * REG + col;
-          const int s2p = ((c + 2) & (MROWS - 1)) * REG + col;
-          const T* ph = S.phi;
-          const T* lp = S.lap;
-          // fourth-order 5x5 gradient of p^i - p^w: the combination (4 D_h - D_2h)/3
-          // of the isotropic 3x3 gradient D_h at spacings ds and 2 ds
-          const T px = (ph[sc + 1] - ph[sc - 1]) * T(4.0 / 9.0) +
-                       (ph[sp + 1] - ph[sp - 1] + ph[sm + 1] - ph[sm - 1]) * T(1.0 / 9.0) -
-                       (ph[sc + 2] - ph[sc - 2]) * T(1.0 / 18.0) -
-                       (ph[s2p + 2] - ph[s2p - 2] + ph[s2m + 2] - ph[s2m - 2]) * T(1.0 / 72.0);
-          const T py = (ph[sp] - ph[sm]) * T(4.0 / 9.0) +
-                       (ph[sp + 1] - ph[sm + 1] + ph[sp - 1] - ph[sm - 1]) * T(1.0 / 9.0) -
-                       (ph[s2p] - ph[s2m]) * T(1.0 / 18.0) -
-                       (ph[s2p + 2] - ph[s2m + 2] + ph[s2p - 2] - ph[s2m - 2]) * T(1.0 / 72.0);
-          // isotropic 3x3 gradient of the Laplacian:
-          // [ (q(+1,0)-q(-1,0))/3 + (diagonal differences)/12 ] / ds
-          const T lx = (lp[sc + 1] - lp[sc - 1]) * T(1.0 / 3.0) +
-                       (lp[sp + 1] - lp[sp - 1] + lp[sm + 1] - lp[sm - 1]) * T(1.0 / 12.0);
-          const T ly = (lp[sp] - lp[sm]) * T(1.0 / 3.0) +
-                       (lp[sp + 1] - lp[sm + 1] + lp[sp - 1] - lp[sm - 1]) * T(1.0 / 12.0);
-          const T rho = S.rho[sc], ux = S.ux[sc], uy = S.uy[sc], drho = S.drho[sc];
-          const T ir = rcp(rho);
-          const T gdx = P.dt * P.inv_ds * (px * ir + P.kappa * lx);
-          const T gdy = P.dt * P.inv_ds * (py * ir + P.kappa * ly);
-          if (!(rho > T(0)) || !(rho < T(1e30))) atomicOr(P.err, 1u);
-          const T e = T(1) - T(0.5) * (ux * ux + uy * uy);
-          const T h = gdx * ux + gdy * uy;
-          const T p0 = P.omega * drho * ir + P.omega * (e - T(1)) - h;
-          const T p1 = e - P.Tt + T(1);
-          const T p2 = P.omega * e - h;
-          const T lo = P.xlo, hi = P.xhi;
-          const T mxu[2] = {lo * ux, hi * ux}, myu[2] = {lo * uy, hi * uy};
-          const T mxg[2] = {lo * gdx, hi * gdx}, myg[2] = {lo * gdy, hi * gdy};
-
-          T f[16];
-          const T* src = S.fs + (c & (FROWS - 1)) * 16 * REG + col;
+        if (P.regularize) {
+          // Eq. (ereg): replace f* by f^eq + w [H2:A2/2 + H3:A3/6], A_n = sum f^neq xi^n
+          T m2xx = 0, m2xy = 0, m2yy = 0, m3xxx = 0, m3xxy = 0, m3xyy = 0, m3yyy = 0;
 #pragma unroll
-          for (int kk = 0; kk < 16; ++kk) f[kk] = src[kk * REG];
-
-          T base[16];
-#pragma unroll
-          for (int kk = 0; kk < 16; ++kk) base[kk] = f[kk];
-          if (P.regularize) {
-            // Eq. (ereg): replace f* by f^eq + w [H2:A2/2 + H3:A3/6], A_n = sum f^neq xi^n
-            T m2xx = 0, m2xy = 0, m2yy = 0, m3xxx = 0, m3xxy = 0, m3xyy = 0, m3yyy = 0;
-#pragma unroll
-            for (int kk = 0; kk < 16; ++kk) {
-              const T x = P.v[kk].xi_x, y = P.v[kk].xi_y, fv = f[kk];
-              m2xx += fv * x * x;
-              m2xy += fv * x * y;
-              m2yy += fv * y * y;
-              m3xxx += fv * x * x * x;
-              m3xxy += fv * x * x * y;
-              m3xyy += fv * x * y * y;
-              m3yyy += fv * y * y * y;
-            }
-            const T Tt = P.Tt;
-            const T A2xx = m2xx + P.rho_ref - rho * (ux * ux + Tt);
-            const T A2xy = m2xy - rho * ux * uy;
-            const T A2yy = m2yy + P.rho_ref - rho * (uy * uy + Tt);
-            const T A3xxx = m3xxx - rho * (ux * ux * ux + T(3) * Tt * ux);
-            const T A3xxy = m3xxy - rho * (ux * ux * uy + Tt * uy);
-            const T A3xyy = m3xyy - rho * (ux * uy * uy + Tt * ux);
-            const T A3yyy = m3yyy - rho * (uy * uy * uy + T(3) * Tt * uy);
-#pragma unroll
-            for (int kk = 0; kk < 16; ++kk) {
-              const VelConst<T>& v = P.v[kk];
-              const ClassConst<T>& cl = P.cls[kk >> 2];
-              const T cu = v.xi_x * ux + v.xi_y * uy;
-              // f^eq - w rho_ref = w [ (rho - rho_ref) + rho (P_k - 1) ]
-              const T pm1 = (e - T(1) + cl.Ak) + cu * ((e + cl.Bk) + cu * (T(0.5) + cu / T(6)));
-              const T feqs = v.w * (drho + rho * pm1);
-              const T fneq = v.w * (v.r2xx * A2xx + v.r2xy * A2xy + v.r2yy * A2yy +
-                                    v.r3xxx * A3xxx + v.r3xxy * A3xxy + v.r3xyy * A3xyy +
-                                    v.r3yyy * A3yyy);
-              base[kk] = feqs + fneq;
-            }
+          for (int kk = 0; kk < 16; ++kk) {
+            const T x = P.v[kk].xi_x, y = P.v[kk].xi_y, fv = f[kk];
+            m2xx += fv * x * x;
+            m2xy += fv * x * y;
+            m2yy += fv * y * y;
+            m3xxx += fv * x * x * x;
+            m3xxy += fv * x * x * y;
+            m3xyy += fv * x * y * y;
+            m3yyy += fv * y * y * y;
           }
-          T scale = T(1);
-          if (P.reservoir) {
-            const T dx = T(p4_x) - P.cxc, dy = T(c) - P.cyc;
-            if (dx * dx + dy * dy > P.rbc2) scale = P.rho_ext * ir;
-          }
-
-          rho_post = scale * rho;  // the collision conserves mass; the reservoir rescales it
-          ST* dst = static_cast<ST*>(P.fout) + (long long)c * Lx + p4_x;
-          const long long pl = P.plane;
-          const T add = P.reservoir ? P.rho_ref * (scale - T(1)) : T(0);
-          if (!P.reservoir) scale = T(1);
+          const T Tt = P.Tt;
+          const T A2xx = m2xx + P.rho_ref - rho * (ux * ux + Tt);
+          const T A2xy = m2xy - rho * ux * uy;
+          const T A2yy = m2yy + P.rho_ref - rho * (uy * uy + Tt);
+          const T A3xxx = m3xxx - rho * (ux * ux * ux + T(3) * Tt * ux);
+          const T A3xxy = m3xxy - rho * (ux * ux * uy + Tt * uy);
+          const T A3xyy = m3xyy - rho * (ux * uy * uy + Tt * ux);
+          const T A3yyy = m3yyy - rho * (uy * uy * uy + T(3) * Tt * uy);
 #pragma unroll
-          for (int grp = 0; grp < 4; ++grp) {
-            const ClassConst<T>& cl = P.cls[grp];
-            const int ix = grp & 1, iy = grp >> 1;  // magnitude index (0 lo, 1 hi) in x, y
-            const T P0 = p0 + cl.omA, P1 = p1 + cl.Ak, K1c = p2 + cl.omB, wr = cl.w * rho;
-            const T sw = scale * wr, radd = cl.w * add;
-            const T s1 = scale * P.one_m_omega;
-            // opposite velocities (sign patterns s and s + 2) differ only in
-            // the sign of xi.u and xi.g: split the cubic into its even and odd
-            // parts E and O, so that poly(+) = E + O and poly(-) = E - O
-            T outv[4];
-#pragma unroll
-            for (int sgn = 0; sgn < 2; ++sgn) {
-              const int kk = 4 * grp + sgn;
-              const bool nx = sgn == 1;
-              const T cu = (nx ? -mxu[ix] : mxu[ix]) + myu[iy];  // xi.u
-              const T D = (nx ? -mxg[ix] : mxg[ix]) + myg[iy];   // dt xi.g
-              // poly = K0 + cu (K1 + cu (K2 + cu om/6)) with K0 = D P1 + P0,
-              // K1 = K1c + D, K2 = D/2 + om/2: the cubic in xi.u of
-              // (omega f^eq + dt F_k - omega w rho_ref) / (w rho)
-              const T c2 = cu * cu;
-              const T E = c2 * P.om2 + (cu * D + P0);
-              const T O = cu * (c2 * P.om6 + K1c) + D * (c2 * T(0.5) + P1);
-              // f^{n+1} = (1 - omega) f* + w rho poly, then the reservoir rescale
-              // s f + w rho_ref (s - 1) outside R_BC (s = 1, add = 0 elsewhere)
-              const T Q = sw * E + radd;
-              outv[sgn] = s1 * base[kk] + (sw * O + Q);
-              outv[sgn + 2] = s1 * base[kk + 2] + (Q - sw * O);
-            }
-#pragma unroll
-            for (int sgn = 0; sgn < 4; ++sgn) {
-              *dst = to_store<ST, T>(outv[sgn]);
-              dst += pl;
-            }
+          for (int kk = 0; kk < 16; ++kk) {
+            const VelConst<T>& v = P.v[kk];
+            const ClassConst<T>& cl = P.cls[kk >> 2];
+            const T cu = v.xi_x * ux + v.xi_y * uy;
+            // f^eq - w rho_ref = w [ (rho - rho_ref) + rho (P_k - 1) ]
+            const T pm1 = (e - T(1) + cl.Ak) + cu * ((e + cl.Bk) + cu * (T(0.5) + cu / T(6)));
+            const T feqs = v.w * (drho + rho * pm1);
+            const T fneq = v.w * (v.r2xx * A2xx + v.r2xy * A2xy + v.r2yy * A2yy +
+                                  v.r3xxx * A3xxx + v.r3xxy * A3xxy + v.r3xyy * A3xyy +
+                                  v.r3yyy * A3yyy);
+            f[kk] = feqs + fneq;
           }
         }
-        if (DIAG) {  // fused diagnostics: mass per thread, bubble sites per warp
-          const bool on = rho_post >= T(0);
-          const bool in = on && rho_post < P.diag_thr;
-          if (on) {
-            dseg += rho_post - P.rho_ref;
-            ++nseg;
+
+        // f^{n+1} = (1 - omega) f* + w rho poly; opposite velocities (sign
+        // patterns s and s + 2) differ only in the sign of xi.u and xi.g: the
+        // cubic splits into even and odd parts E and O, poly(+-) = E +- O
+        T outv[16];
+#pragma unroll
+        for (int grp = 0; grp < 4; ++grp) {
+          const ClassConst<T>& cl = P.cls[grp];
+          const int ix = grp & 1, iy = grp >> 1;  // magnitude index (0 lo, 1 hi) in x, y
+          const T P0 = p0 + cl.omA, P1 = p1 + cl.Ak, K1c = p2 + cl.omB, sw = cl.w * rho;
+#pragma unroll
+          for (int sgn = 0; sgn < 2; ++sgn) {
+            const int kk = 4 * grp + sgn;
+            const bool nx = sgn == 1;
+            const T cu = (nx ? -mxu[ix] : mxu[ix]) + myu[iy];  // xi.u
+            const T D = (nx ? -mxg[ix] : mxg[ix]) + myg[iy];   // dt xi.g
+            // poly = K0 + cu (K1 + cu (K2 + cu om/6)) with K0 = D P1 + P0,
+            // K1 = K1c + D, K2 = D/2 + om/2: the cubic in xi.u of
+            // (omega f^eq + dt F_k - omega w rho_ref) / (w rho)
+            const T c2 = cu * cu;
+            const T E = c2 * P.om2 + (cu * D + P0);
+            const T O = cu * (c2 * P.om6 + K1c) + D * (c2 * T(0.5) + P1);
+            const T Q = sw * E;
+            outv[kk] = fma(P.one_m_omega, f[kk], fma(sw, O, Q));
+            outv[kk + 2] = fma(P.one_m_omega, f[kk + 2], fma(-sw, O, Q));
           }
-          if (__ballot_sync(0xffffffffu, in)) {  // bubble sites are rare: sum them only here
-            const unsigned long long i = in ? (unsigned long long)p4_x : 0ULL;
-            const unsigned long long j = in ? (unsigned long long)c : 0ULL;
-            unsigned long long v[6] = {in ? 1ULL : 0ULL, i, j, i * i, i * j, j * j};
+        }
+        rho_post = rho;  // the collision conserves mass
+        if (P.reservoir) {
+          // Sec. III A: outside R_BC the node is rescaled to rho_ext: f -> s f,
+          // stored deviation s (f - w rho_ref) + w rho_ref (s - 1)
+          const T dx = T(x4) - P.cxc, dy = T(c) - P.cyc;
+          if (dx * dx + dy * dy > P.rbc2) {
+            const T s = P.rho_ext * ir;
+            rho_post = s * rho;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
+            for (int kk = 0; kk < 16; ++kk)
+              outv[kk] = fma(s, outv[kk], P.cls[kk >> 2].w * P.rho_ref * (s - T(1)));
+          }
+        }
+        if (tstore) {
+          ST* dst = S.out + ((it & 1) * RPI + r4) * (16 * TW) + o4;
 #pragma unroll
-              for (int t = 0; t < 6; ++t) v[t] += __shfl_down_sync(0xffffffffu, v[t], o);
-            }
-            if (lane == 0) {
+          for (int kk = 0; kk < 16; ++kk) dst[kk * TW] = to_store<ST, T>(outv[kk]);
+        } else {
+          ST* dst = static_cast<ST*>(P.fout) + (long long)c * Lx + x4;
+          const long long pl = P.plane;
 #pragma unroll
-              for (int t = 0; t < 6; ++t) atomicAdd(&S.dsums[t], v[t]);
-            }
+          for (int kk = 0; kk < 16; ++kk) dst[kk * pl] = to_store<ST, T>(outv[kk]);
+        }
+      }
+      if (DIAG) {  // fused diagnostics: mass per thread, bubble sites per warp
+        const bool on = rho_post >= T(0);
+        const bool in = on && rho_post < P.diag_thr;
+        if (on) {
+          dseg += rho_post - P.rho_ref;
+          ++nseg;
+        }
+        if (__ballot_sync(0xffffffffu, in)) {  // bubble sites are rare: sum them only here
+          const unsigned long long ii = in ? (unsigned long long)x4 : 0ULL;
+          const unsigned long long jj = in ? (unsigned long long)c : 0ULL;
+          unsigned long long v[6] = {in ? 1ULL : 0ULL, ii, jj, ii * ii, ii * jj, jj * jj};
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int t = 0; t < 6; ++t) v[t] += __shfl_down_sync(0xffffffffu, v[t], o);
+          }
+          if (lane == 0) {
+#pragma unroll
+            for (int t = 0; t < 6; ++t) atomicAdd(&S.dsums[t], v[t]);
           }
         }
       }
     }
-    cp_async_wait<0>();
-    if (DIAG) dmass += (double)dseg + (double)P.rho_ref * (double)nseg;
+    if (tstore) fence_proxy_async();  // the tile's generic writes before its tensor store
+    __syncthreads();
   }
+  // the last tile of the segment
+  if (tstore && tid == 0) {
+    const int it = nit - 1;
+    const int row0 = ys + RPI * (it - WARM);
+    const ST* tile = S.out + (it & 1) * (RPI * 16 * TW);
+    if (row0 + RPI <= ye) {
+      tma_store_rows(tm + 2, strip * TW, row0, tile);
+    } else {
+      for (int r = 0; row0 + r < ye; ++r)
+        tma_store_rows(tm + 3, strip * TW, row0 + r, tile + r * 16 * TW);
+    }
+    bulk_commit();
+  }
+  cp_async_wait<0>();
+  gb = g0 + (unsigned)nit;
+  if (DIAG) dmass += (double)dseg + (double)P.rho_ref * (double)nseg;
 }
 
 // Work items are (row block, strip) pairs in row-block-major order, claimed
@@ -602,6 +645,34 @@ __device__ __forceinline__ void retire_cta(unsigned long long* sched) {
   }
 }
 
+// Before the CTA leaves: every tensor store has completed, and every staged
+// batch it armed has landed.  Normally all were waited for; after a timed-out
+// wait (abort = first such batch + 1) the batches from that one up to the
+// last armed may still be in flight into this CTA's shared memory, and thread
+// 0 waits for each again, bounded, so that no copy outlives the CTA unless
+// the copy engine itself is stuck.
+template <typename SM>
+__device__ __forceinline__ void drain_copies(const SM& S, unsigned armed) {
+  if (threadIdx.x == 0) {
+    bulk_wait_all();
+    const int a = *reinterpret_cast<volatile int*>(S.abort);
+    if (a > 0)
+      for (unsigned b = (unsigned)(a - 1); b < armed; ++b)
+        mbar_wait_bounded(S.bar + (b & 1u), (b >> 1) & 1u, 2000000000ULL);
+  }
+}
+
+__device__ __forceinline__ void init_cta_barriers(unsigned long long* dsums,
+                                                  unsigned long long* bar, int* abort) {
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < 6; ++t) dsums[t] = 0ULL;
+    *abort = 0;
+    mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+}
+
 // DIAG: fuse the diagnostics of the state after the step (P.diag_mass and
 // P.diag_sums receive them); a separate instantiation so that the plain step
 // executes none of their instructions.
@@ -611,15 +682,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const Smem<T, ST> S(smem_raw);
   __shared__ long long s_item;
-  if (threadIdx.x == 0) {
-    for (int t = 0; t < 6; ++t) S.dsums[t] = 0ULL;
-    *S.abort = 0;
-    mbar_init(S.bar, 1);
-    mbar_init(S.bar + 1, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-  }
-  const CUtensorMap* tm = P.tma_ok ? maps.m : nullptr;
-  unsigned batch = 0;  // tensor-copy batches issued (and consumed) by this CTA
+  init_cta_barriers(S.dsums, S.bar, S.abort);
+  const CUtensorMap* tm = maps.m;
+  unsigned gb = 0;     // staged batches of this CTA so far (ring slot g & 1, phase (g >> 1) & 1)
+  unsigned gi = 0;     // thread 0: batches armed on the mbarriers
   double dmass = 0.0;  // fused diagnostics: this thread's mass over all its segments
   for (;;) {
     const long long item = claim_item(P.sched, &s_item);
@@ -628,7 +694,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     const int strip = (int)(item - rb * P.nstrip);
     const int ys = (int)(rb * P.row_block);
     const int ye = min(P.Ly, ys + P.row_block);
-    run_segment<T, ST, ORDER, LIM, VEC, DIAG>(P, S, strip, ys, ye, tm, batch, dmass);
+    run_segment<T, ST, ORDER, LIM, VEC, DIAG>(P, S, strip, ys, ye, tm, gb, gi, dmass);
   }
   if (DIAG) {
     // one warp sum and one global add per warp for the mass; claim_item's
@@ -639,19 +705,21 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     if (threadIdx.x == 0)
       for (int t = 0; t < 6; ++t) atomicAdd(&P.diag_sums[t], S.dsums[t]);
   }
+  drain_copies(S, gi);
   retire_cta(P.sched);
 }
 
 // Several lattices advanced by one launch: their work items are concatenated
-// and claimed from one counter.
+// and claimed from one counter; each lattice brings its own tensor maps.
 template <typename T, int ORDER, int LIM, bool VEC>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     step_batch_kernel(const __grid_constant__ BatchArgs<T> B) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const Smem<T, T> S(smem_raw);
   __shared__ long long s_item;
+  init_cta_barriers(S.dsums, S.bar, S.abort);
   int i = 0;
-  unsigned batch = 0;  // unused: batched lattices stage by per-thread copies
+  unsigned gb = 0, gi = 0;
   double dmass = 0.0;  // unused: batched launches carry no fused diagnostics
   for (;;) {
     const long long item = claim_item(B.sched, &s_item);
@@ -663,7 +731,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     const int strip = (int)(local - rb * P.nstrip);
     const int ys = (int)(rb * P.row_block);
     const int ye = min(P.Ly, ys + P.row_block);
-    run_segment<T, T, ORDER, LIM, VEC, false>(P, S, strip, ys, ye, nullptr, batch, dmass);
+    run_segment<T, T, ORDER, LIM, VEC, false>(P, S, strip, ys, ye, B.maps[i].m, gb, gi, dmass);
   }
+  drain_copies(S, gi);
   retire_cta(B.sched);
 }

@@ -186,12 +186,13 @@ int lbm_histogram(lbm_handle* h, int32_t nbins, double lo, double hi, int64_t* c
 /* ---- allocation-free histogram (the paper has no counterpart) ----------------
  * Same counts as lbm_histogram, for distributions the caller holds in device
  * memory, without allocating anything.  It exists for callers that cannot
- * call cudaMalloc or any allocating routine: code that runs while a stream is
- * captured into a CUDA graph, services whose device memory is owned by
- * another allocator or fully budgeted in advance, and callers that keep f in
- * their own buffers with no lbm_handle.  (lbm_histogram allocates a device
- * counts buffer on every call.)
- *   f_device : device pointer, [16][Ly][Lx], FP64 f when precision is LBM_FP64,
+ * call cudaMalloc or any allocating routine: services whose device memory is
+ * owned by another allocator or fully budgeted in advance, loops that cannot
+ * afford the device synchronisation an allocation may imply, and callers
+ * that keep f in their own buffers with no lbm_handle.  (lbm_histogram
+ * allocates a device counts buffer on every call.)
+ *   f_device : device pointer on the current device (another device returns
+ *              LBM_ERR_INVALID_ARG), [16][Ly][Lx], FP64 f when precision is LBM_FP64,
  *              float (f - w_k rho_ref) when it is LBM_FP32_SHIFTED, IEEE half
  *              (f - w_k rho_ref) when it is LBM_FP16_SHIFTED
  *   nbins    : 1 .. LBM_NOALLOC_MAX_BINS; more returns LBM_ERR_INVALID_ARG
@@ -204,7 +205,9 @@ int lbm_histogram(lbm_handle* h, int32_t nbins, double lo, double hi, int64_t* c
  * All calls share that array, so calls that overlap on the GPU (different
  * streams or threads) race: issue them one after another.  The first call on
  * a device looks up the array's device address (once per device, with that
- * device current); make that first call before any stream capture begins.
+ * device current) and keeps it while the library is loaded, so the device's
+ * context must not be reset (cudaDeviceReset) in between; make that first
+ * call before any stream capture begins.
  * Returns LBM_ERR_INVALID_ARG for bad arguments, LBM_ERR_CUDA if a CUDA call
  * fails. */
 #define LBM_NOALLOC_MAX_BINS 4096

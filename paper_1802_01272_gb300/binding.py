@@ -238,10 +238,11 @@ def histogram_noalloc(f, precision: int, rho_ref: float, nbins: int, lo: float, 
             and f.dim() == 3 and f.shape[0] == 16):
         raise ValueError(f"expected a contiguous {want} CUDA tensor of shape [16, Ly, Lx]")
     counts = np.zeros(nbins, dtype=np.int64)
-    _check(lib().lbm_histogram_noalloc(C.c_void_p(f.data_ptr()), f.shape[2], f.shape[1],
-                                       precision, rho_ref, nbins, lo, hi, _stream_ptr(stream),
-                                       counts.ctypes.data_as(C.POINTER(C.c_int64))),
-           "lbm_histogram_noalloc")
+    with torch.cuda.device(f.device):  # the library counts on the current device
+        _check(lib().lbm_histogram_noalloc(C.c_void_p(f.data_ptr()), f.shape[2], f.shape[1],
+                                           precision, rho_ref, nbins, lo, hi, _stream_ptr(stream),
+                                           counts.ctypes.data_as(C.POINTER(C.c_int64))),
+               "lbm_histogram_noalloc")
     return counts
 
 

@@ -2,13 +2,13 @@
 // allocates no memory.
 //
 // Who needs it: callers that must not call cudaMalloc or any allocating
-// routine -- code running while a stream is being captured into a CUDA graph
-// (where an allocation would break the capture), processes whose device
-// memory is handed out by another allocator or reserved up front (a serving
-// loop that keeps every lattice resident and has budgeted all of HBM), and
-// callers that keep f in their own buffers without a lbm_handle.
-// lbm_histogram needs a temporary device counts buffer on every call; this
-// variant counts into a fixed, file-scope device array instead.
+// routine -- processes whose device memory is handed out by another
+// allocator or reserved up front (a serving loop that keeps every lattice
+// resident and has budgeted all of HBM), loops that cannot afford the device
+// synchronisation an allocation may imply, and callers that keep f in their
+// own buffers without a lbm_handle.  lbm_histogram needs a temporary device
+// counts buffer on every call; this variant counts into a fixed, file-scope
+// device array instead.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -30,7 +30,9 @@ std::mutex g_mutex;
 void* g_bins_addr[kMaxDevices] = {nullptr};
 
 // The array's name is only a host-side stand-in; the device address is
-// looked up once per device, with that device current.
+// looked up once per device, with that device current, and kept for the life
+// of the process: it assumes the device's context is not reset
+// (cudaDeviceReset) while the library is loaded.
 int bins_address(int device, unsigned long long** out) {
   if (device < 0 || device >= kMaxDevices) return LBM_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_mutex);
@@ -55,6 +57,12 @@ extern "C" int lbm_histogram_noalloc(const void* f_device, int32_t Lx, int32_t L
     return LBM_ERR_INVALID_ARG;
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess) return LBM_ERR_CUDA;
+  // the bins live on the current device: f must be there too
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, f_device) != cudaSuccess) return LBM_ERR_INVALID_ARG;
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+    return LBM_ERR_INVALID_ARG;
+  if (attr.device != device) return LBM_ERR_INVALID_ARG;
   unsigned long long* bins = nullptr;
   const int r = bins_address(device, &bins);
   if (r != LBM_OK) return r;

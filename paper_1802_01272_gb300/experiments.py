@@ -102,19 +102,36 @@ def planar_interface_sigma(T=0.8, kappa=1e-4, ds=1 / 256, Lx=512, Ly=8, tau=1e-3
     return kappa * float(np.sum(grad * grad)) * ds / 2.0, prof
 
 
+def slab_plateaus(prof):
+    """Bulk densities of the slab profile of planar_interface_sigma (liquid on
+    [Lx/4, 3Lx/4), vapour outside, periodic): the medians over windows of
+    Lx/8 + 1 nodes centred on the liquid's middle (Lx/2) and the vapour's
+    (node 0), a quarter of the lattice from either interface, so that the
+    over- and undershoots next to a diffuse interface stay out.
+    Returns (rho_L, rho_V)."""
+    prof = np.asarray(prof, dtype=np.float64)
+    n = len(prof)
+    hw = n // 16
+    idx = np.arange(-hw, hw + 1)
+    return float(np.median(prof[(n // 2 + idx) % n])), float(np.median(prof[idx % n]))
+
+
 def phase_diagram(temperatures, kappa=1e-4, ds=1 / 256, tau=1e-3, Lx=128, t_end=20.0,
                   precision=LBM_FP32_SHIFTED, stream=None):
     """Sec. II E's liquid-vapour phase diagram from relaxed planar interfaces:
     for each T, the liquid and vapour plateau densities of a slab (periodic x,
-    `Lx` nodes, relaxed to t_end) beside the Maxwell values.  Returns a list of
-    dicts with T, rho_L, rho_V, maxwell_L, maxwell_V and sigma."""
+    `Lx` nodes, relaxed to t_end; slab_plateaus) beside the Maxwell values.
+    Returns a list of dicts with T, rho_L, rho_V (plateaus), rho_max, rho_min
+    (the profile's extremes), maxwell_L, maxwell_V and sigma."""
     out = []
     for T in temperatures:
         sigma, prof = planar_interface_sigma(T=T, kappa=kappa, ds=ds, Lx=Lx, tau=tau,
                                              t_end=t_end, precision=precision, stream=stream)
         rl, rv = eos.coexistence(T)
-        out.append({"T": float(T), "rho_L": float(prof.max()), "rho_V": float(prof.min()),
-                    "maxwell_L": rl, "maxwell_V": rv, "sigma": sigma})
+        pl, pv = slab_plateaus(prof)
+        out.append({"T": float(T), "rho_L": pl, "rho_V": pv, "rho_max": float(prof.max()),
+                    "rho_min": float(prof.min()), "maxwell_L": rl, "maxwell_V": rv,
+                    "sigma": sigma})
     return out
 
 

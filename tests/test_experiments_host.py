@@ -97,3 +97,20 @@ def test_phase_diagram_driver_plumbing(monkeypatch):
         rl, rv = eos.coexistence(r["T"])
         assert r["maxwell_L"] == rl and r["maxwell_V"] == rv
         assert r["rho_L"] == rl and abs(r["rho_V"] / rv - 0.9) < 1e-12
+        assert r["rho_max"] == rl and r["rho_min"] == r["rho_V"]
+
+
+def test_slab_plateaus_ignore_interface_overshoot():
+    """The plateau reader takes medians over the bulk of each phase: an
+    overshoot next to an interface (which the extremes would report) and a
+    spike one node wide inside the window do not move it."""
+    from paper_1802_01272_gb300 import experiments as X
+    n = 128
+    x = np.arange(n, dtype=np.float64)
+    prof = 0.3 + 0.8 * (np.tanh((x - n / 4) / 2.0) - np.tanh((x - 3 * n / 4) / 2.0))
+    prof[n // 4 + 6] += 0.05      # overshoot on the liquid side of an interface
+    prof[3 * n // 4 + 6] -= 0.05  # undershoot on the vapour side
+    prof[n // 2 + 1] += 0.2       # a one-node spike inside the liquid window
+    pl, pv = X.slab_plateaus(prof)
+    assert abs(pl - 1.9) < 1e-9 and abs(pv - 0.3) < 1e-9  # tanh tails
+    assert prof.max() > 1.9 + 0.1 and prof.min() < 0.3 - 0.04

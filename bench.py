@@ -94,8 +94,8 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = ("lbm_kernels.cuh", "step_kernel_body.cuh", "step_fp32.cu", "step_fp64.cu",
-                  "step_fp16.cu")
+KERNEL_SOURCES = ("lbm_kernels.cuh", "step_kernel_body.cuh", "step_select.cuh", "step_fp32.cu",
+                  "step_fp64.cu", "step_fp16.cu")
 
 
 def kernel_source_hash():
@@ -106,6 +106,7 @@ def kernel_source_hash():
 
 
 E2E_REPS = 5  # repetitions of the end-to-end region (median reported)
+RUNS, RUN_S = 5, 1.0  # repeated device-resident regions (median and spread reported)
 
 
 def ncu_record(workload):
@@ -324,8 +325,10 @@ def main():
                     help="fix the row-block height (2 CTAs per SM) instead of tuning")
     ap.add_argument("--cpu-baseline-only", type=float, default=None, metavar="SECONDS",
                     help="print the oracle's host-core sample for this workload and exit")
-    ap.add_argument("--server", type=int, default=0, metavar="NJOBS",
-                    help="also run the sweep-server comparison over NJOBS config-5 jobs")
+    ap.add_argument("--no-repeats", action="store_true",
+                    help="skip the repeated >= 1 s regions (profiling runs)")
+    ap.add_argument("--server", type=int, default=24, metavar="NJOBS",
+                    help="sweep-server comparison over NJOBS config-5 jobs (0: off)")
     ap.add_argument("--server-step-scale", type=float, default=0.05)
     ap.add_argument("--ctu-order", type=int, default=None, help="override the scheme (profiling)")
     ap.add_argument("--limiter", type=int, default=None, help="override the limiter (profiling)")
@@ -390,11 +393,24 @@ def main():
     e1.record(stream)
     barrier()
     ms = e0.elapsed_time(e1)
+    # repeats: RUNS more regions of at least RUN_S seconds each (at least K
+    # steps), for the median and spread of the step time
+    per_step = ms / args.steps
+    rep_steps = max(args.steps, int(RUN_S * 1e3 / max(per_step, 1e-6)) + 1)
+    run_ms = []
+    for _ in range(RUNS if not args.no_repeats else 0):
+        barrier()
+        e0.record(stream)
+        L.step(rep_steps)
+        e1.record(stream)
+        barrier()
+        run_ms.append(max_over_ranks(e0.elapsed_time(e1)))
     clk = clocks.stop()
     L.sync()
     ms = max_over_ranks(ms)
     ms_per_step = ms / args.steps
     value = world * nodes * args.steps / (ms * 1e-3) / 1e9
+    runs = [world * nodes * rep_steps / (m * 1e-3) / 1e9 for m in run_ms]
 
     # roofline of the step kernel: the only kernel in the timed region
     peak, peak_kind = load_peaks()
@@ -473,7 +489,7 @@ def main():
     L.close()
 
     srv = None
-    if args.server:
+    if args.server and world == 1:
         srv = run_server_bench(P, stream, args.server, args.server_step_scale)
 
     cb = None
@@ -503,6 +519,9 @@ def main():
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                          if peak_kind == "measured" else "fallback 6.8 TB/s",
                          "algorithmic_bytes_per_launch": alg_bytes},
+            "runs": {"steps_each": rep_steps, "glups": runs,
+                     "median": statistics.median(runs) if runs else None,
+                     "spread": (max(runs) - min(runs)) / statistics.median(runs) if runs else None},
             "issue_roofline": issue_roof,
             "fp32_roofline": fp32_roof,
             "gpu_launches": args.steps,

@@ -41,7 +41,7 @@ struct lbm_handle {
   StepArgs<float> a32;
   StepArgs<double> a64;
   // tensor maps of the step from f[c] to f[1 - c]: loads of f[c] (RPI-row and
-  // 1-row staging boxes), stores into f[1 - c] (RPI-row and 1-row output tiles)
+  // 1-row staging boxes), stores of output tiles into f[1 - c]
   RowMaps tmap[2];
   // CUDA graphs of GRAPH_STEPS consecutive steps starting from f[0] / f[1]
   // (built on first use, rebuilt when the launch geometry changes)
@@ -93,11 +93,11 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// f [16][Ly][Lx] as a 3-D tensor ordered (x, plane, row), moved in boxes of
+// f [16][Ly][Lx] as a 3-D tensor ordered (x, plane, row), read in boxes of
 // `cols` columns x 16 planes x `rows` rows: a box is [rows][16][cols] in
-// shared memory (the staging ring's rows, or the collision's output tile).
-// False when the encoder is unavailable or rejects the layout (the kernel then
-// stages every strip by per-thread copies, or stores per thread).
+// shared memory (consecutive rows of the staging ring).  False when the
+// encoder is unavailable or rejects the layout (the kernel then stages every
+// strip by per-thread copies).
 bool encode_row_map(void* base, size_t elem, int Lx, int Ly, int cols, int rows,
                     CUtensorMap* out) {
   const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
@@ -111,6 +111,25 @@ bool encode_row_map(void* base, size_t elem, int Lx, int Ly, int cols, int rows,
                                                : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   return enc(out, type, 3,
              base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// f [16][Ly][Lx] as a 3-D tensor ordered (x, row, plane), written in tiles of
+// TW columns x RPI rows x 16 planes: a tile is [16][RPI][TW] in shared memory
+// (the collision's plane-major output tile).  False when the encoder is
+// unavailable or rejects the layout (the kernel then stores per thread).
+bool encode_tile_map(void* base, size_t elem, int Lx, int Ly, CUtensorMap* out) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || Lx < TW || Ly < RPI) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)Lx, (cuuint64_t)Ly, 16};
+  const cuuint64_t strides[2] = {(cuuint64_t)Lx * elem, (cuuint64_t)Lx * (cuuint64_t)Ly * elem};
+  const cuuint32_t box[3] = {(cuuint32_t)TW, (cuuint32_t)RPI, 16};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUtensorMapDataType type = elem == 8   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                   : elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  return enc(out, type, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -370,16 +389,28 @@ int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out) {
   cudaMemsetAsync(h->d_err, 0, sizeof(unsigned int), h->stream);
   cudaMemsetAsync(h->d_sched, 0, 2 * sizeof(unsigned long long), h->stream);
 
+  // tensor maps: rows of f^n staged by tensor copies (row strides and the
+  // staging window's start must be 16-byte multiples: Lx a multiple of 4
+  // values, 8 for half), output tiles stored by tensor stores
+  std::memset(h->tmap, 0, sizeof(h->tmap));
+  bool tin = (p->Lx % (h->elem == 2 ? 8 : 4)) == 0, tout = tin;
+  const int scol = h->elem == 2 ? scol_of<__half>() : scol_of<float>();
+  for (int i = 0; i < 2; ++i) {
+    tin = tin && encode_row_map(h->f[i], h->elem, p->Lx, p->Ly, scol, RPI, &h->tmap[i].m[0]) &&
+          encode_row_map(h->f[i], h->elem, p->Lx, p->Ly, scol, 1, &h->tmap[i].m[1]);
+    tout = tout && encode_tile_map(h->f[1 - i], h->elem, p->Lx, p->Ly, &h->tmap[i].m[2]);
+  }
+  h->vec = tin;  // else every strip stages by per-thread loads
+
   // launch geometry: strips of TW output columns, rows split evenly over a
   // persistent grid of (SMs x resident CTAs), at least 48 rows per CTA
   h->nstrip = (p->Lx + TW - 1) / TW;
-  // 16-byte copies of staging groups: 4 columns (float, double) or 8 (half)
-  h->vec = (p->Lx % (h->elem == 2 ? 8 : 4)) == 0;
   h->smem = step_smem_bytes(h->elem, h->elem == 8 ? 8 : 4);
   const int lim = p->ctu_order == 1 ? 0 : p->limiter;
-  int occ = h->elem == 4   ? step_occupancy_f32(p->ctu_order, lim, h->vec, h->smem)
-            : h->elem == 2 ? step_occupancy_f16(p->ctu_order, lim, h->vec, h->smem)
-                           : step_occupancy_f64(p->ctu_order, lim, h->vec, h->smem);
+  const bool regu = p->regularize != 0;
+  int occ = h->elem == 4   ? step_occupancy_f32(p->ctu_order, lim, h->vec, regu, h->smem)
+            : h->elem == 2 ? step_occupancy_f16(p->ctu_order, lim, h->vec, regu, h->smem)
+                           : step_occupancy_f64(p->ctu_order, lim, h->vec, regu, h->smem);
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
   if (occ < 1 || nsm < 1) {
@@ -407,15 +438,6 @@ int lbm_create(const lbm_params* p, void* cuda_stream, lbm_handle** out) {
     fill_step_args<double>(h, h->a64);
   else
     fill_step_args<float>(h, h->a32);
-  std::memset(h->tmap, 0, sizeof(h->tmap));
-  bool tin = h->vec, tout = h->vec;
-  for (int i = 0; i < 2; ++i) {
-    tin = tin && encode_row_map(h->f[i], h->elem, p->Lx, p->Ly, SCOL, RPI, &h->tmap[i].m[0]) &&
-          encode_row_map(h->f[i], h->elem, p->Lx, p->Ly, SCOL, 1, &h->tmap[i].m[1]);
-    tout = tout &&
-           encode_row_map(h->f[1 - i], h->elem, p->Lx, p->Ly, TW, RPI, &h->tmap[i].m[2]) &&
-           encode_row_map(h->f[1 - i], h->elem, p->Lx, p->Ly, TW, 1, &h->tmap[i].m[3]);
-  }
   h->a32.tma_in = h->a64.tma_in = tin;
   h->a32.tma_out = h->a64.tma_out = tout;
   AuxArgs& x = h->aux;
@@ -558,9 +580,10 @@ cudaError_t launch_one(lbm_handle* h, int c, int lim) {
 // on any stream, the legacy default stream included.  nullptr on failure.
 cudaGraphExec_t build_graph(lbm_handle* h, int c, int lim) {
   const bool f32 = h->elem != 8;
-  void* fn = h->elem == 8   ? step_kernel_ptr_f64(h->p.ctu_order, lim, h->vec)
-             : h->elem == 4 ? step_kernel_ptr_f32(h->p.ctu_order, lim, h->vec)
-                            : step_kernel_ptr_f16(h->p.ctu_order, lim, h->vec);
+  const bool regu = h->p.regularize != 0;
+  void* fn = h->elem == 8   ? step_kernel_ptr_f64(h->p.ctu_order, lim, h->vec, regu)
+             : h->elem == 4 ? step_kernel_ptr_f32(h->p.ctu_order, lim, h->vec, regu)
+                            : step_kernel_ptr_f16(h->p.ctu_order, lim, h->vec, regu);
   cudaGraph_t g = nullptr;
   if (cudaGraphCreate(&g, 0) != cudaSuccess) return nullptr;
   cudaGraphNode_t prev = nullptr;
@@ -631,9 +654,11 @@ int lbm_set_launch(lbm_handle* h, int32_t row_block, int32_t ctas_per_sm) {
   const int lim = h->p.ctu_order == 1 ? 0 : h->p.limiter;
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
-  const int occ = h->elem == 4   ? step_occupancy_f32(h->p.ctu_order, lim, h->vec, h->smem)
-                  : h->elem == 2 ? step_occupancy_f16(h->p.ctu_order, lim, h->vec, h->smem)
-                                 : step_occupancy_f64(h->p.ctu_order, lim, h->vec, h->smem);
+  const bool regu = h->p.regularize != 0;
+  const int occ =
+      h->elem == 4   ? step_occupancy_f32(h->p.ctu_order, lim, h->vec, regu, h->smem)
+      : h->elem == 2 ? step_occupancy_f16(h->p.ctu_order, lim, h->vec, regu, h->smem)
+                     : step_occupancy_f64(h->p.ctu_order, lim, h->vec, regu, h->smem);
   if (nsm < 1 || occ < 1) return set_err(h, LBM_ERR_CUDA);
   if (ctas_per_sm > occ) return LBM_ERR_INVALID_ARG;
   const long long items = (long long)((h->p.Ly + row_block - 1) / row_block) * h->nstrip;
@@ -651,9 +676,11 @@ int lbm_tune(lbm_handle* h, int32_t steps_per_trial, lbm_kernel_info* out) {
   const int lim = h->p.ctu_order == 1 ? 0 : h->p.limiter;
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
-  const int occ = h->elem == 4   ? step_occupancy_f32(h->p.ctu_order, lim, h->vec, h->smem)
-                  : h->elem == 2 ? step_occupancy_f16(h->p.ctu_order, lim, h->vec, h->smem)
-                                 : step_occupancy_f64(h->p.ctu_order, lim, h->vec, h->smem);
+  const bool regu = h->p.regularize != 0;
+  const int occ =
+      h->elem == 4   ? step_occupancy_f32(h->p.ctu_order, lim, h->vec, regu, h->smem)
+      : h->elem == 2 ? step_occupancy_f16(h->p.ctu_order, lim, h->vec, regu, h->smem)
+                     : step_occupancy_f64(h->p.ctu_order, lim, h->vec, regu, h->smem);
   if (nsm < 1 || occ < 1) return set_err(h, LBM_ERR_CUDA);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -735,8 +762,8 @@ int lbm_step_many(lbm_handle* const* handles, int32_t count, int64_t n) {
     for (int j = 0; j < i; ++j)
       if (handles[j] == h) return LBM_ERR_INVALID_ARG;  // each lattice once
   }
-  // Lattices that cannot share a launch (FP64 storage, another scheme or
-  // limiter, the scalar column path) step on their own, one launch per step.
+  // Lattices that cannot share a launch (FP64 or FP16 storage, another scheme,
+  // limiter or collision, no tensor maps) step on their own.
   lbm_handle* group[MAXB];
   int ng = 0;
   auto flush = [&](int64_t steps) -> int {
@@ -747,7 +774,8 @@ int lbm_step_many(lbm_handle* const* handles, int32_t count, int64_t n) {
     }
     int grid_max = 0;
     {
-      int occ = step_batch_occupancy_f32(h0->p.ctu_order, lim0, true, group[0]->smem);
+      int occ = step_batch_occupancy_f32(h0->p.ctu_order, lim0, h0->p.regularize != 0,
+                                         group[0]->smem);
       int nsm = 0;
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h0->device);
       grid_max = occ * nsm;
@@ -772,23 +800,70 @@ int lbm_step_many(lbm_handle* const* handles, int32_t count, int64_t n) {
     }
     b.item_start[ng] = total;
     const int g = (int)(total < grid_max ? total : grid_max);
-    for (int64_t s = 0; s < steps; ++s) {
+    const bool regu = h0->p.regularize != 0;
+    // the arguments of the batched step `s` steps ahead of the lattices' state
+    auto args_for = [&](int s) {
       for (int i = 0; i < ng; ++i) {
         lbm_handle* h = group[i];
+        const int c = (h->cur + s) & 1;
         b.L[i] = h->a32;
         b.L[i].row_block = rbs[i];
         b.L[i].items = its[i];
-        b.L[i].fin = static_cast<const float*>(h->f[h->cur]);
-        b.L[i].fout = static_cast<float*>(h->f[1 - h->cur]);
-        b.maps[i] = h->tmap[h->cur];
+        b.L[i].fin = static_cast<const float*>(h->f[c]);
+        b.L[i].fout = static_cast<float*>(h->f[1 - c]);
+        b.maps[i] = h->tmap[c];
       }
-      cudaError_t e = launch_step_batch_f32(b, h0->p.ctu_order, lim0, true, g, group[0]->smem,
+    };
+    auto advance = [&](int64_t k) {
+      for (int i = 0; i < ng; ++i) {
+        group[i]->cur = (int)((group[i]->cur + k) & 1);
+        group[i]->steps += k;
+      }
+    };
+    // long runs: GRAPH_STEPS batched steps per graph launch (built for this
+    // group, explicit kernel nodes, so any stream works)
+    if (steps >= 3 * GRAPH_STEPS) {
+      cudaGraph_t gr = nullptr;
+      cudaGraphExec_t ex = nullptr;
+      bool ok = cudaGraphCreate(&gr, 0) == cudaSuccess;
+      cudaGraphNode_t prev = nullptr;
+      void* fn = step_batch_kernel_ptr_f32(h0->p.ctu_order, lim0, regu);
+      for (int s = 0; s < GRAPH_STEPS && ok; ++s) {
+        args_for(s);
+        void* kargs[1] = {&b};
+        cudaKernelNodeParams kp{};
+        kp.func = fn;
+        kp.gridDim = dim3(g);
+        kp.blockDim = dim3(NT);
+        kp.sharedMemBytes = (unsigned)group[0]->smem;
+        kp.kernelParams = kargs;  // copied into the node
+        cudaGraphNode_t node = nullptr;
+        ok = cudaGraphAddKernelNode(&node, gr, prev ? &prev : nullptr, prev ? 1 : 0, &kp) ==
+             cudaSuccess;
+        prev = node;
+      }
+      if (ok) ok = cudaGraphInstantiate(&ex, gr, 0) == cudaSuccess;
+      if (gr) cudaGraphDestroy(gr);
+      if (ok) {
+        for (; steps >= GRAPH_STEPS; steps -= GRAPH_STEPS) {
+          const cudaError_t e = cudaGraphLaunch(ex, h0->stream);
+          if (e != cudaSuccess) {
+            cudaGraphExecDestroy(ex);
+            return cuda_check(h0, e);
+          }
+          advance(GRAPH_STEPS);  // an even count: every lattice's buffer parity returns
+        }
+        cudaGraphExecDestroy(ex);
+      } else if (ex) {
+        cudaGraphExecDestroy(ex);
+      }
+    }
+    for (int64_t s = 0; s < steps; ++s) {
+      args_for(0);
+      cudaError_t e = launch_step_batch_f32(b, h0->p.ctu_order, lim0, regu, g, group[0]->smem,
                                             h0->stream);
       if (e != cudaSuccess) return cuda_check(h0, e);
-      for (int i = 0; i < ng; ++i) {
-        group[i]->cur ^= 1;
-        group[i]->steps += 1;
-      }
+      advance(1);
     }
     ng = 0;
     return LBM_OK;
@@ -797,6 +872,7 @@ int lbm_step_many(lbm_handle* const* handles, int32_t count, int64_t n) {
     lbm_handle* h = handles[i];
     const int lim = h->p.ctu_order == 1 ? 0 : h->p.limiter;
     const bool batchable = h->elem == 4 && h->vec && h->p.ctu_order == h0->p.ctu_order &&
+                           h->p.regularize == h0->p.regularize &&
                            lim == lim0;
     if (!batchable) {
       int r = lbm_step(h, n);

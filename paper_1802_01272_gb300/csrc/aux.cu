@@ -285,13 +285,14 @@ cudaError_t launch_hist(const AuxArgs& a, const void* f, int nbins, double lo, d
 }
 
 size_t step_smem_bytes(size_t stage_elem, size_t elem) {
-  const size_t elems = (size_t)FROWS * 16 * REG + 6 * (size_t)MROWS * REG;
-  // + 128 bytes to align the staging ring and the output tiles for tensor
-  // copies; ints, the fused diagnostics' bubble-site sums, two mbarriers and
-  // the CTA's wait-abort flag
-  return 128 + stage_elem * ((size_t)SROWS * 16 * SCOL + 2 * (size_t)RPI * 16 * TW) +
-         elem * elems + sizeof(int) * (SG + (SG & 1)) + 6 * sizeof(unsigned long long) +
-         2 * sizeof(unsigned long long) + 2 * sizeof(int);
+  const size_t elems = (size_t)FROWS * FRS + 6 * (size_t)MROWS * MP;
+  // + 128 bytes to align the staging ring and the output tile for tensor
+  // copies; the fused diagnostics' bubble-site sums, the staging slots'
+  // mbarriers and the CTA's wait-abort flag
+  const size_t scol = stage_elem == 2 ? scol_of<__half>() : scol_of<float>();
+  return 128 + stage_elem * ((size_t)NSLOT * RPI * 16 * scol + (size_t)RPI * 16 * TW) +
+         elem * elems + 6 * sizeof(unsigned long long) + NSLOT * sizeof(unsigned long long) +
+         2 * sizeof(int);
 }
 
 }  // namespace ctulbm

@@ -22,8 +22,8 @@ struct AuxArgs {
   float xif[16][2], wf[16];  // the same tables rounded to float on the host
 };
 
-// One fused step kernel: returns cudaSuccess or the launch error.
-// `maps` describe a.fin (RowMaps); they are read only when a.tma_ok.
+// One fused step kernel: returns cudaSuccess or the launch error.  `vec`: the
+// lattice has tensor maps (`maps`, for a.fin and a.fout) and stages by them.
 cudaError_t launch_step_f32(const StepArgs<float>& a, const RowMaps& maps, int order, int lim,
                             bool vec, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_step_f64(const StepArgs<double>& a, const RowMaps& maps, int order, int lim,
@@ -31,19 +31,23 @@ cudaError_t launch_step_f64(const StepArgs<double>& a, const RowMaps& maps, int 
 // FP16 shifted storage, FP32 arithmetic (a.fin / a.fout hold half).
 cudaError_t launch_step_f16(const StepArgs<float>& a, const RowMaps& maps, int order, int lim,
                             bool vec, int grid, size_t smem, cudaStream_t s);
-// Several FP32 lattices in one launch (same scheme, limiter and column path).
-cudaError_t launch_step_batch_f32(const BatchArgs<float>& b, int order, int lim, bool vec,
+// Several FP32 lattices in one launch (same scheme, limiter and collision;
+// every lattice has tensor maps).
+cudaError_t launch_step_batch_f32(const BatchArgs<float>& b, int order, int lim, bool regu,
                                   int grid, size_t smem, cudaStream_t s);
-int step_batch_occupancy_f32(int order, int lim, bool vec, size_t smem);
+int step_batch_occupancy_f32(int order, int lim, bool regu, size_t smem);
+// The batched kernel (for CUDA graph kernel nodes; its attribute is set by
+// step_batch_occupancy_f32).
+void* step_batch_kernel_ptr_f32(int order, int lim, bool regu);
 // Largest resident CTAs per SM for the selected step kernel (0 on error).
-int step_occupancy_f32(int order, int lim, bool vec, size_t smem);
-int step_occupancy_f64(int order, int lim, bool vec, size_t smem);
-int step_occupancy_f16(int order, int lim, bool vec, size_t smem);
+int step_occupancy_f32(int order, int lim, bool vec, bool regu, size_t smem);
+int step_occupancy_f64(int order, int lim, bool vec, bool regu, size_t smem);
+int step_occupancy_f16(int order, int lim, bool vec, bool regu, size_t smem);
 // The step kernel a launch_step_* call would run (for CUDA graph kernel nodes,
 // whose parameters are (StepArgs, RowMaps) as in a direct launch).
-void* step_kernel_ptr_f32(int order, int lim, bool vec);
-void* step_kernel_ptr_f64(int order, int lim, bool vec);
-void* step_kernel_ptr_f16(int order, int lim, bool vec);
+void* step_kernel_ptr_f32(int order, int lim, bool vec, bool regu);
+void* step_kernel_ptr_f64(int order, int lim, bool vec, bool regu);
+void* step_kernel_ptr_f16(int order, int lim, bool vec, bool regu);
 
 // Dynamic shared memory of the step kernel: staging ring in the storage type
 // (stage_elem bytes per value), the other rings in the arithmetic type.

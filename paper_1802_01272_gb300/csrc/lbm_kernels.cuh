@@ -16,15 +16,17 @@
 // force stencil needs on each side, and two more that complete the groups.
 // Warps hold one sign quadrant (sgn xi_x, sgn xi_y), so the upwind side of
 // every stencil is a compile-time constant inside a warp.  Iteration i takes
-// the staged rows n = B_i .. B_i + 3 of f^n (one tensor copy of 72 columns x
-// 16 planes x 4 rows, issued one iteration ahead into a two-slot ring) and
+// the staged rows n = B_i .. B_i + 3 of f^n (one tensor copy of 68 columns x
+// 16 planes x 4 rows, issued two iterations ahead into a three-slot ring by a
+// producer thread whose warp has no collision work) and
 //   P1  advects them (every quadrant emits the rows n - 2, two rows behind
 //       the staged one) into a ring of advected rows f*;
 //   P2  one thread per node: rho*, u*, p^i - p^w of those rows;
 //   P3  the 9-point Laplacian of rho* one row further back;
-//   P4  224 threads, one per output node, two rows further back: gradients
-//       -> g, f^eq + dt F_k, relaxation of all 16 planes into an output tile
-//       that one thread writes to f^{n+1} with a tensor store.
+//   P4  224 threads, one per output node, two rows further back (warp w:
+//       columns 8w .. 8w+7 of the four rows): gradients -> g, f^eq + dt F_k,
+//       relaxation of all 16 planes into a plane-major output tile that one
+//       thread writes to f^{n+1} with a tensor store.
 // Four CTA barriers per four rows; every shared-memory offset inside an
 // iteration is a compile-time constant from a per-thread base.  f^n is read
 // from HBM once per step (the halo columns of neighbouring strips are L2
@@ -44,12 +46,25 @@ constexpr int TW = REG - 8;     // output columns per strip (56: strips start on
 constexpr int XOFF = 4;         // region column of the strip's first output column
 constexpr int NT = 16 * NG;     // threads per CTA
 constexpr int RPI = 4;          // rows per pipeline iteration (one staged batch)
-constexpr int SG = NG + 2;      // staging groups per plane row: region plus one group per side
-constexpr int SCOL = 4 * SG;    // staging columns per plane row
-constexpr int SROWS = 2 * RPI;  // staging ring: the batch being read and the one being loaded
+// Staging columns per plane row: the region plus the advection halo.  A thread
+// of column group g reads staging columns 4g + 2 .. 4g + 8 (s_x > 0 uses
+// 4g + 2 .. 4g + 7); column 68 is needed only by the last group of s_x < 0,
+// whose results there (region columns 62, 63) feed no output.  68 columns
+// are whole 16-byte chunks for float and double; half rows need 72.
+template <typename ST>
+constexpr int scol_of() {
+  return sizeof(ST) == 2 ? 72 : 68;
+}
+constexpr int NSLOT = 3;        // staging ring: the batch being read, two being loaded
+constexpr int PRODUCER = NT - 32;  // the thread that issues tensor copies and stores (warp 7,
+                                   // which has no node in the collision phase)
 constexpr int FROWS = 8;        // advected-row ring f* (power of two)
 constexpr int MROWS = 8;        // moment rings (power of two)
 constexpr int P4T = RPI * TW;   // collision threads: one per output node of an iteration
+// Padded pitches: the collision's warps read 4 rows x 8 columns of the rings;
+// row strides of 8 mod 32 words put the four rows on distinct banks.
+constexpr int MP = REG + 8;           // moment rings: words per row
+constexpr int FRS = 16 * REG + 8;     // advected-row ring: words per row (16 planes of REG)
 constexpr int WARM = 2;         // iterations of a segment before its first output row
 
 // Per-velocity constants, computed on the host in FP64 and rounded to T.
@@ -100,11 +115,11 @@ struct StepArgs {
   VelConst<T> v[16];
 };
 
-// f^n and f^{n+1} as 3-D tensors (x, plane, row): m[0] loads boxes of SCOL
-// columns x 16 planes x RPI rows of fin, m[1] single rows; m[2] stores boxes
-// of TW columns x 16 planes x RPI rows into fout, m[3] single rows.
+// f^n as a 3-D tensor (x, plane, row): m[0] loads boxes of scol_of<ST>()
+// columns x 16 planes x RPI rows of fin, m[1] single rows; f^{n+1} as (x, row, plane):
+// m[2] stores tiles of TW columns x RPI rows x 16 planes into fout.
 struct RowMaps {
-  CUtensorMap m[4];
+  CUtensorMap m[3];
 };
 
 constexpr int MAXB = 12;  // lattices per batched launch (kernel parameter space)
@@ -363,6 +378,193 @@ __device__ __forceinline__ void advect_row(AdvState<T>& s, const ST* srow, const
     s.Z1[i] = Z[i];
   }
 }
+
+// ------------------------------------------- packed FP32 advection (FP32 and FP16 storage)
+// The same row update on column pairs (0, 1) and (2, 3) held as float2: every
+// operation whose operands are whole pairs runs as one packed FP32x2
+// instruction (sm_100+), which issues once for two lanes' worth of work; the
+// jumps R^x (pairs shifted by one column), the limiters (min/max have no
+// packed form) and the neighbour-shifted terms stay scalar.  Numerically each
+// component is the scalar operation (round to nearest), except h^x, taken as
+// (f(i) - f(i-2))/4 for s_x > 0 (the same quantity as (R^x(i) + R^x(i-1))/4).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;"
+      : "=l"(r)
+      : "l"(*reinterpret_cast<const unsigned long long*>(&a)),
+        "l"(*reinterpret_cast<const unsigned long long*>(&b)));
+  return *reinterpret_cast<const float2*>(&r);
+}
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+
+// the MC half-limited jump with h = (R + Ru)/4 given (see half_limited)
+template <int LIM>
+__device__ __forceinline__ float mc_half(float R, float Ru, float h) {
+  if constexpr (LIM == 1) {
+    return 0.0f;
+  } else if constexpr (LIM == 2) {
+    return 0.5f * R;
+  } else {
+    return min_xorsign_abs(fmaxf(min_xorsign_abs(R, Ru), 0.0f), h);
+  }
+}
+
+struct AdvState2 {
+  float2 Fp[2], Ryp[2], Syp[2], Z1[2], Z2[2], pend[2];  // as AdvState, column pairs
+};
+
+// per-thread constant pairs of the packed row update
+struct VelPairs {
+  float2 ncx, nax, cy, by0, q;  // (-/+)c_x (sign of -s_x), -ax, c_y, by0, 1/4
+  float by1;
+};
+template <int SX>
+__device__ __forceinline__ VelPairs vel_pairs(const VelConst<float>& c) {
+  VelPairs v;
+  v.ncx = dup2(SX > 0 ? -c.cx : c.cx);
+  v.nax = dup2(-c.ax);
+  v.cy = dup2(c.cy);
+  v.by0 = dup2(c.by0);
+  v.q = dup2(0.25f);
+  v.by1 = c.by1;
+  return v;
+}
+
+template <typename ST>
+__device__ __forceinline__ float2 sload2(const ST* p) {
+  if constexpr (sizeof(ST) == 4) return *reinterpret_cast<const float2*>(p);
+  else return __half22float2(*reinterpret_cast<const __half2*>(p));
+}
+template <typename ST>
+__device__ __forceinline__ void sload4p(const ST* p, float2& a, float2& b) {
+  if constexpr (sizeof(ST) == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    a = make_float2(t.x, t.y);
+    b = make_float2(t.z, t.w);
+  } else {
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+    b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+  }
+}
+
+template <int SX, int SY, int ORDER, int LIM, typename ST>
+__device__ __forceinline__ void advect_row2(AdvState2& s, const ST* srow, const VelPairs& c,
+                                            float* out) {
+  float2 B0, B1;  // columns (0, 1), (2, 3)
+  sload4p<ST>(srow, B0, B1);
+  float2 Z[2];
+  if constexpr (SX > 0) {
+    const float2 A = sload2<ST>(srow - 2);  // columns (-2, -1)
+    const float R_1 = A.y - A.x, R0 = B0.x - A.y, R1 = B0.y - B0.x;
+    const float R2 = B1.x - B0.y, R3 = B1.y - B1.x;
+    const float2 X01 = fma2(c.ncx, make_float2(R0, R1), B0);
+    const float2 X23 = fma2(c.ncx, make_float2(R2, R3), B1);
+    if constexpr (ORDER == 2) {
+      const float2 h01 = mul2(c.q, sub2(B0, A)), h23 = mul2(c.q, sub2(B1, B0));
+      const float S0 = mc_half<LIM>(R0, R_1, h01.x), S1 = mc_half<LIM>(R1, R0, h01.y);
+      const float S2 = mc_half<LIM>(R2, R1, h23.x), S3 = mc_half<LIM>(R3, R2, h23.y);
+      const float S4 = shfl_dn1(S0);
+      Z[0] = fma2(c.nax, make_float2(S1 - S0, S2 - S1), X01);
+      Z[1] = fma2(c.nax, make_float2(S3 - S2, S4 - S3), X23);
+    } else {
+      Z[0] = X01;
+      Z[1] = X23;
+    }
+  } else {
+    const float a = from_store<ST, float>(srow[-1]), e = from_store<ST, float>(srow[4]);
+    const float R0 = B0.x - a, R1 = B0.y - B0.x, R2 = B1.x - B0.y;
+    const float R3 = B1.y - B1.x, R4 = e - B1.y;
+    const float2 X01 = fma2(c.ncx, make_float2(R1, R2), B0);
+    const float2 X23 = fma2(c.ncx, make_float2(R3, R4), B1);
+    if constexpr (ORDER == 2) {
+      const float S0 = mc_half<LIM>(R0, R1, 0.25f * (R0 + R1));
+      const float S1 = mc_half<LIM>(R1, R2, 0.25f * (R1 + R2));
+      const float S2 = mc_half<LIM>(R2, R3, 0.25f * (R2 + R3));
+      const float S3 = mc_half<LIM>(R3, R4, 0.25f * (R3 + R4));
+      const float S4 = shfl_dn1(S0);
+      Z[0] = fma2(c.nax, make_float2(S1 - S0, S2 - S1), X01);
+      Z[1] = fma2(c.nax, make_float2(S3 - S2, S4 - S3), X23);
+    } else {
+      Z[0] = X01;
+      Z[1] = X23;
+    }
+  }
+
+  float2 o[2];
+  const float2 Bn[2] = {B0, B1};
+  if constexpr (ORDER == 2) {
+    float2 Ry[2], Sy[2], dSy[2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      Ry[m] = sub2(Bn[m], s.Fp[m]);
+      const float2 hy = mul2(c.q, add2(Ry[m], s.Ryp[m]));
+      if constexpr (SY > 0)
+        Sy[m] = make_float2(mc_half<LIM>(Ry[m].x, s.Ryp[m].x, hy.x),
+                            mc_half<LIM>(Ry[m].y, s.Ryp[m].y, hy.y));
+      else
+        Sy[m] = make_float2(mc_half<LIM>(s.Ryp[m].x, Ry[m].x, hy.x),
+                            mc_half<LIM>(s.Ryp[m].y, Ry[m].y, hy.y));
+      dSy[m] = sub2(Sy[m], s.Syp[m]);
+    }
+    // dS^y one column upwind in x
+    float2 dsu[2];
+    if constexpr (SX > 0) {
+      const float du = shfl_up1(dSy[1].y);
+      dsu[0] = make_float2(du, dSy[0].x);
+      dsu[1] = make_float2(dSy[0].y, dSy[1].x);
+    } else {
+      const float du = shfl_dn1(dSy[0].x);
+      dsu[0] = make_float2(dSy[0].y, dSy[1].x);
+      dsu[1] = make_float2(dSy[1].y, du);
+    }
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const float2 Zi = SY > 0 ? s.Z1[m] : s.Z2[m];
+      const float2 Zu = SY > 0 ? s.Z2[m] : s.Z1[m];
+      float2 v = fma2(c.cy, sub2(Zu, Zi), Zi);
+      v = fma2(c.by0, dSy[m], v);
+      o[m] = make_float2(fmaf(c.by1, dsu[m].x, v.x), fmaf(c.by1, dsu[m].y, v.y));
+      s.Ryp[m] = Ry[m];
+      s.Syp[m] = Sy[m];
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const float2 Zi = SY > 0 ? s.Z1[m] : s.Z2[m];
+      const float2 Zu = SY > 0 ? s.Z2[m] : s.Z1[m];
+      o[m] = fma2(c.cy, sub2(Zu, Zi), Zi);
+    }
+  }
+
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    if constexpr (SY > 0) {
+      out[2 * m] = s.pend[m].x;
+      out[2 * m + 1] = s.pend[m].y;
+      s.pend[m] = o[m];
+    } else {
+      out[2 * m] = o[m].x;
+      out[2 * m + 1] = o[m].y;
+    }
+    s.Fp[m] = Bn[m];
+    s.Z2[m] = s.Z1[m];
+    s.Z1[m] = Z[m];
+  }
+}
+
+// the advection state of the arithmetic type: FP32 packs column pairs
+template <typename T>
+struct AdvSel {
+  using State = AdvState<T>;
+};
+template <>
+struct AdvSel<float> {
+  using State = AdvState2;
+};
 
 #include "step_kernel_body.cuh"
 

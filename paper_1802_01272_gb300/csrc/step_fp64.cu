@@ -3,53 +3,21 @@
 
 namespace ctulbm {
 
-namespace {
-template <int ORDER, int LIM, bool VEC, bool DIAG>
-void* kernel_ptr() {
-  return reinterpret_cast<void*>(&step_kernel<double, double, ORDER, LIM, VEC, DIAG>);
-}
+#include "step_select.cuh"
 
-template <bool DIAG>
-void* select_d(int order, int lim, bool vec) {
-  if (order == 1) return vec ? kernel_ptr<1, 0, true, DIAG>() : kernel_ptr<1, 0, false, DIAG>();
-  switch (lim) {
-    case 1: return vec ? kernel_ptr<2, 1, true, DIAG>() : kernel_ptr<2, 1, false, DIAG>();
-    case 2: return vec ? kernel_ptr<2, 2, true, DIAG>() : kernel_ptr<2, 2, false, DIAG>();
-    default: return vec ? kernel_ptr<2, 0, true, DIAG>() : kernel_ptr<2, 0, false, DIAG>();
-  }
-}
-
-// the variant with fused diagnostics is a separate kernel, so the plain step
-// carries none of their instructions
-void* select(int order, int lim, bool vec, bool diag) {
-  return diag ? select_d<true>(order, lim, vec) : select_d<false>(order, lim, vec);
-}
-}  // namespace
+using Sel64 = StepSelect<double, double>;
 
 cudaError_t launch_step_f64(const StepArgs<double>& a, const RowMaps& maps, int order, int lim,
                             bool vec, int grid, size_t smem, cudaStream_t s) {
-  // the shared-memory attribute was set by step_occupancy_* when the handle was made
-  void* fn = select(order, lim, vec, a.diag_mass != nullptr);
-  void* args[] = {const_cast<StepArgs<double>*>(&a), const_cast<RowMaps*>(&maps)};
-  return cudaLaunchKernel(fn, dim3(grid), dim3(NT), args, smem, s);
+  return Sel64::launch(a, maps, order, lim, vec, grid, smem, s);
 }
 
-void* step_kernel_ptr_f64(int order, int lim, bool vec) { return select(order, lim, vec, false); }
+void* step_kernel_ptr_f64(int order, int lim, bool vec, bool regu) {
+  return Sel64::select(order, lim, vec, false, regu);
+}
 
-// Sets the shared-memory attribute of both variants (with and without fused
-// diagnostics); returns the CTAs per SM both reach.
-int step_occupancy_f64(int order, int lim, bool vec, size_t smem) {
-  int occ = 1 << 30;
-  for (int d = 0; d < 2; ++d) {
-    void* fn = select(order, lim, vec, d == 1);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return 0;
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, NT, smem) != cudaSuccess) return 0;
-    occ = n < occ ? n : occ;
-  }
-  return occ;
+int step_occupancy_f64(int order, int lim, bool vec, bool regu, size_t smem) {
+  return Sel64::occupancy(order, lim, vec, regu, smem);
 }
 
 }  // namespace ctulbm

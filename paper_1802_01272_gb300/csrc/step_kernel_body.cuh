@@ -1,24 +1,11 @@
 // step_kernel_body.cuh -- the fused CTU step kernel (included by lbm_kernels.cuh
 // inside namespace ctulbm).  See the layout notes at the top of lbm_kernels.cuh.
 
-// ------------------------------------------------------------ async copies
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 // ------------------------------------- tensor copies, stores and mbarriers
-// A staged batch (RPI rows of SCOL columns x 16 planes) arrives by one tensor
-// copy into a ring slot laid out [RPI][16][SCOL]; completion is counted in
-// bytes on the slot's mbarrier, and every wait on it is bounded in time.  The
-// collision's output tile [RPI][16][TW] leaves by one tensor store.
+// A staged batch (RPI rows of scol_of<ST>() columns x 16 planes) arrives by one
+// tensor copy into a ring slot laid out [RPI][16][columns]; completion is
+// counted in bytes on the slot's mbarrier, and every wait on it is bounded in
+// time.  The collision's output tile [16][RPI][TW] leaves by one tensor store.
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
 }
@@ -69,13 +56,13 @@ __device__ __forceinline__ void tma_load_rows(void* dst, const CUtensorMap* map,
       "l"(map), "r"(x), "r"(0), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
-// One tensor store of the tile at `src` to rows y.. of the (x, plane, row) tensor.
+// One tensor store of the tile at `src` to rows y.. of the (x, row, plane) tensor.
 __device__ __forceinline__ void tma_store_rows(const CUtensorMap* map, int x, int y,
                                                const void* src) {
   asm volatile(
       "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(
           map),
-      "r"(x), "r"(0), "r"(y), "r"(smem_u32(src))
+      "r"(x), "r"(y), "r"(0), "r"(smem_u32(src))
       : "memory");
 }
 __device__ __forceinline__ void bulk_commit() {
@@ -100,60 +87,56 @@ __device__ __forceinline__ int mod_pos(int a, int n) {  // a mod n for a > -n*10
 // then ints.  All moment rings are indexed by lattice row mod MROWS.
 template <typename T, typename ST>
 struct Smem {
-  ST* stage;  // [2][RPI][16][SCOL] f^n rows of the strip, one group of halo per side
-  ST* out;    // [2][RPI][16][TW] f^{n+1} tiles for the tensor store
-  T* fs;      // [FROWS][16][REG] advected f*
-  T* rho;     // [MROWS][REG]
+  static constexpr int SCOL = scol_of<ST>();
+  ST* stage;  // [NSLOT][RPI][16][SCOL] f^n rows of the strip, with the advection halo
+  ST* out;    // [16][RPI][TW] the f^{n+1} tile of the tensor store (plane-major)
+  T* fs;      // [FROWS][FRS] advected f*: 16 planes of REG per row, padded
+  T* rho;     // [MROWS][MP]
   T* drho;    // rho* - rho_ref
   T* ux;
   T* uy;
   T* phi;     // p^i - p^w
   T* lap;     // 9-point Laplacian of rho*
-  int* col;   // [SG] wrapped global column of each staging group
   unsigned long long* dsums;  // [6] fused diagnostics: per-CTA bubble-site sums
-  unsigned long long* bar;    // [2] mbarriers of the staging slots
+  unsigned long long* bar;    // [NSLOT] mbarriers of the staging slots
   int* abort;                 // a bounded wait of this CTA timed out: stop waiting
   __device__ Smem(unsigned char* raw) {
     // tensor copies need 128-byte aligned tiles; the allocation has the slack
     raw += (128u - ((unsigned)__cvta_generic_to_shared(raw) & 127u)) & 127u;
     stage = reinterpret_cast<ST*>(raw);
-    out = stage + SROWS * 16 * SCOL;
-    T* p = reinterpret_cast<T*>(out + 2 * RPI * 16 * TW);
+    out = stage + NSLOT * RPI * 16 * SCOL;
+    T* p = reinterpret_cast<T*>(out + RPI * 16 * TW);
     fs = p;
-    p += FROWS * 16 * REG;
+    p += FROWS * FRS;
     rho = p;
-    drho = rho + MROWS * REG;
-    ux = drho + MROWS * REG;
-    uy = ux + MROWS * REG;
-    phi = uy + MROWS * REG;
-    lap = phi + MROWS * REG;
-    col = reinterpret_cast<int*>(lap + MROWS * REG);
-    dsums = reinterpret_cast<unsigned long long*>(col + SG + (SG & 1));  // 8-byte aligned
+    drho = rho + MROWS * MP;
+    ux = drho + MROWS * MP;
+    uy = ux + MROWS * MP;
+    phi = uy + MROWS * MP;
+    lap = phi + MROWS * MP;
+    dsums = reinterpret_cast<unsigned long long*>(lap + MROWS * MP);  // 8-byte aligned
     bar = dsums + 6;
-    abort = reinterpret_cast<int*>(bar + 2);
+    abort = reinterpret_cast<int*>(bar + NSLOT);
   }
 };
 
-// Per-thread copies of staged rows (strips at the periodic x seam, lattices
-// without tensor maps): a staged row holds 16 planes x CH 16-byte chunks;
-// thread t copies chunks t, t + NT, ..., so its (plane, column) slots are
-// fixed for a whole segment.
+// Per-thread staging (lattices without tensor maps) and wall ghost rows: a
+// staged row holds 16 planes x CH chunks of EPC values; thread t handles
+// chunks t, t + NT, ..., so its (plane, column) slots are fixed for a segment.
 template <typename T, typename ST>
 struct StageSlots {
+  static constexpr int SCOL = scol_of<ST>();
   static constexpr int CH = SCOL * (int)sizeof(ST) / 16;  // 16-byte chunks per plane row
   static constexpr int EPC = 16 / (int)sizeof(ST);         // elements per chunk
   static constexpr int PER_ROW = 16 * CH;
   static constexpr int NS = (PER_ROW + NT - 1) / NT;      // chunks per thread per row
-  long long src[NS];  // element offset of the chunk in row 0 of f^n (plane and column)
   int dst[NS];        // element offset inside a staged row
-  __device__ StageSlots(const StepArgs<T>& P, const Smem<T, ST>& S, bool vec) {
+  __device__ StageSlots() {
 #pragma unroll
     for (int m = 0; m < NS; ++m) {
       const int c = threadIdx.x + NT * m;
       const int k = c / CH, ch = c - (c / CH) * CH;
-      const int gg = (ch * EPC) >> 2, within = (ch * EPC) & 3;
       dst[m] = k * SCOL + ch * EPC;
-      src[m] = c < PER_ROW ? (long long)k * P.plane + (vec ? S.col[gg] + within : 0) : 0;
     }
   }
 };
@@ -175,112 +158,173 @@ __device__ __forceinline__ void stage_ghost_row(const StepArgs<T>& P, const Stag
   }
 }
 
-// Issue staged batch `g` (rows r0 .. r0+RPI-1) into ring slot g & 1: one
-// tensor copy (TMA, thread 0) when the batch lies inside the lattice, else
-// one copy per row (periodic wrap in y) and ghost rows written by all threads
-// (walls); per-thread cp.async copies (VEC) or plain loads when the strip
-// cannot use the tensor map.  Every batch arrives once on the slot's mbarrier
-// (with the tensor copies' byte count, zero otherwise), so the barrier's phase
-// parity is (g >> 1) & 1 for every batch.
-template <typename T, typename ST, bool VEC>
-__device__ __forceinline__ void issue_batch(const StepArgs<T>& P, const Smem<T, ST>& S,
-                                            const StageSlots<T, ST>& sl, const CUtensorMap* tm,
-                                            bool tma, int x0, int r0, unsigned g, unsigned& gi) {
-  using SS = StageSlots<T, ST>;
-  constexpr unsigned ROW_BYTES = 16u * SCOL * (unsigned)sizeof(ST);
-  const int Ly = P.Ly;
-  ST* base = S.stage + (g & 1u) * (RPI * 16 * SCOL);
-  unsigned long long* bar = S.bar + (g & 1u);
-  const bool touches_wall = P.walls && (r0 < 0 || r0 + RPI > Ly);
-  if (touches_wall) {
-    for (int r = 0; r < RPI; ++r) {
-      const int row = r0 + r;
-      if (row < 0 || row >= Ly) stage_ghost_row<T, ST>(P, sl, base + r * 16 * SCOL, row < 0);
-    }
-    // these generic writes precede later tensor copies into the same slot
-    fence_proxy_async();
+// Staged batch g (rows r0 .. r0+RPI-1, staging columns x0 .. x0+SCOL-1) lives
+// in ring slot g % NSLOT; every batch arrives once on that slot's mbarrier
+// (with the byte count of its tensor copies, zero otherwise), so the phase it
+// completes has parity (g / NSLOT) & 1.
+__device__ __forceinline__ unsigned slot_of(unsigned g) { return g % NSLOT; }
+__device__ __forceinline__ unsigned parity_of(unsigned g) { return (g / NSLOT) & 1u; }
+
+// Wall ghost rows of batch g (constant per plane), written by all threads.
+template <typename T, typename ST>
+__device__ __forceinline__ void ghost_rows(const StepArgs<T>& P, const Smem<T, ST>& S,
+                                           const StageSlots<T, ST>& sl, int r0, unsigned g) {
+  constexpr int SCOL = Smem<T, ST>::SCOL;
+  if (!(P.walls && (r0 < 0 || r0 + RPI > P.Ly))) return;
+  ST* base = S.stage + slot_of(g) * (RPI * 16 * SCOL);
+  for (int r = 0; r < RPI; ++r) {
+    const int row = r0 + r;
+    if (row < 0 || row >= P.Ly) stage_ghost_row<T, ST>(P, sl, base + r * 16 * SCOL, row < 0);
   }
-  // after a timed-out wait thread 0 arms and issues nothing more: no copy can
-  // then be in flight except the batches armed before (drain_copies waits for them)
-  const bool arm = threadIdx.x == 0 && !*reinterpret_cast<volatile int*>(S.abort);
-  if (arm) gi = g + 1u;
-  if (tma) {
-    if (arm) {
-      if (r0 >= 0 && r0 + RPI <= Ly) {
-        mbar_arrive_expect_tx(bar, RPI * ROW_BYTES);
-        tma_load_rows(base, tm, x0, r0, bar);
-      } else {
-        unsigned bytes = 0;
-        for (int r = 0; r < RPI; ++r)
-          if (!(P.walls && (r0 + r < 0 || r0 + r >= Ly))) bytes += ROW_BYTES;
-        mbar_arrive_expect_tx(bar, bytes);
-        for (int r = 0; r < RPI; ++r) {
-          const int row = r0 + r;
-          if (P.walls && (row < 0 || row >= Ly)) continue;
-          tma_load_rows(base + r * 16 * SCOL, tm + 1, x0, wrapi(row, Ly), bar);
-        }
-      }
-    }
+  // these generic writes precede later tensor copies into the same slot
+  fence_proxy_async();
+}
+
+// Tensor copies of batch g, issued by the producer thread: one copy when the
+// batch lies inside the lattice in y, else one per row (periodic wrap in y;
+// wall ghost rows skipped).  Columns outside [0, Lx) arrive as zeros and
+// seam_fixup replaces them.  After a timed-out wait nothing more is armed or
+// issued: no copy can then be in flight except the batches armed before
+// (drain_copies waits for them).
+template <typename T, typename ST>
+__device__ __forceinline__ void arm_tma(const StepArgs<T>& P, const Smem<T, ST>& S,
+                                        const CUtensorMap* tm, int x0, int r0, unsigned g,
+                                        unsigned& gi) {
+  constexpr int SCOL = Smem<T, ST>::SCOL;
+  constexpr unsigned ROW_BYTES = 16u * SCOL * (unsigned)sizeof(ST);
+  if (*reinterpret_cast<volatile int*>(S.abort)) return;
+  gi = g + 1u;
+  const int Ly = P.Ly;
+  ST* base = S.stage + slot_of(g) * (RPI * 16 * SCOL);
+  unsigned long long* bar = S.bar + slot_of(g);
+  if (r0 >= 0 && r0 + RPI <= Ly) {
+    mbar_arrive_expect_tx(bar, RPI * ROW_BYTES);
+    tma_load_rows(base, tm, x0, r0, bar);
   } else {
+    unsigned bytes = 0;
+    for (int r = 0; r < RPI; ++r)
+      if (!(P.walls && (r0 + r < 0 || r0 + r >= Ly))) bytes += ROW_BYTES;
+    mbar_arrive_expect_tx(bar, bytes);
     for (int r = 0; r < RPI; ++r) {
       const int row = r0 + r;
       if (P.walls && (row < 0 || row >= Ly)) continue;
-      ST* srow = base + r * 16 * SCOL;
-      const ST* frow = static_cast<const ST*>(P.fin) + (long long)wrapi(row, Ly) * P.Lx;
-#pragma unroll
-      for (int m = 0; m < SS::NS; ++m) {
-        const int c = threadIdx.x + NT * m;
-        if (c < SS::PER_ROW) {
-          if (VEC) {
-            cp_async16(srow + sl.dst[m], frow + sl.src[m]);
-          } else {
-            const int k = c / SS::CH, ch = c - k * SS::CH;
-            const ST* fk = frow + (long long)k * P.plane;
-            const int xs = S.col[0];  // unwrapped first staging column (scalar path)
-#pragma unroll
-            for (int e = 0; e < SS::EPC; ++e)
-              srow[sl.dst[m] + e] = __ldg(fk + wrapi(xs + ch * SS::EPC + e, P.Lx));
-          }
-        }
-      }
+      tma_load_rows(base + r * 16 * SCOL, tm + 1, x0, wrapi(row, Ly), bar);
     }
-    if (arm) mbar_arrive_expect_tx(bar, 0u);
   }
-  cp_async_commit();
 }
 
-// Every thread waits for staged batch g (bounded); per-thread copies also need
-// the CTA barrier that makes the other threads' copies visible.  A timeout
+// Lattices without tensor maps: every thread loads its chunks of batch g,
+// wrapping in x and y; the producer arms the slot's barrier with no bytes.
+template <typename T, typename ST>
+__device__ __forceinline__ void load_scalar(const StepArgs<T>& P, const Smem<T, ST>& S,
+                                            const StageSlots<T, ST>& sl, int x0, int r0,
+                                            unsigned g, unsigned& gi) {
+  using SS = StageSlots<T, ST>;
+  constexpr int SCOL = Smem<T, ST>::SCOL;
+  const int Ly = P.Ly;
+  ST* base = S.stage + slot_of(g) * (RPI * 16 * SCOL);
+  for (int r = 0; r < RPI; ++r) {
+    const int row = r0 + r;
+    if (P.walls && (row < 0 || row >= Ly)) continue;
+    ST* srow = base + r * 16 * SCOL;
+    const ST* frow = static_cast<const ST*>(P.fin) + (long long)wrapi(row, Ly) * P.Lx;
+#pragma unroll
+    for (int m = 0; m < SS::NS; ++m) {
+      const int c = threadIdx.x + NT * m;
+      if (c < SS::PER_ROW) {
+        const int k = c / SS::CH, ch = c - k * SS::CH;
+        const ST* fk = frow + (long long)k * P.plane;
+#pragma unroll
+        for (int e = 0; e < SS::EPC; ++e)
+          srow[sl.dst[m] + e] = __ldg(fk + wrapi(x0 + ch * SS::EPC + e, P.Lx));
+      }
+    }
+  }
+  if (threadIdx.x == PRODUCER && !*reinterpret_cast<volatile int*>(S.abort)) {
+    gi = g + 1u;
+    mbar_arrive_expect_tx(S.bar + slot_of(g), 0u);
+  }
+}
+
+// Every thread waits for staged batch g (bounded); per-thread loads also need
+// the CTA barrier that makes the other threads' values visible.  A timeout
 // sets error bit 1 and records the batch (abort = g + 1): the CTA stops
 // waiting and issuing, its results are void.
-template <typename T, typename SM>
-__device__ __forceinline__ void wait_batch(const StepArgs<T>& P, const SM& S, unsigned g,
-                                           bool tma) {
+template <bool VEC, typename T, typename SM>
+__device__ __forceinline__ void wait_batch(const StepArgs<T>& P, const SM& S, unsigned g) {
   if (!*reinterpret_cast<volatile int*>(S.abort)) {
-    if (!mbar_wait_bounded(S.bar + (g & 1u), (g >> 1) & 1u, 1000000000ULL)) {
+    if (!mbar_wait_bounded(S.bar + slot_of(g), parity_of(g), 1000000000ULL)) {
       *reinterpret_cast<volatile int*>(S.abort) = (int)(g + 1u);
       atomicOr(P.err, 2u);
     }
   }
-  if (!tma) {
-    cp_async_wait<1>();
-    __syncthreads();
+  if (!VEC) __syncthreads();
+}
+
+// A strip at the periodic x seam: the tensor copy of batch g filled its
+// staging columns outside [0, Lx) with zeros; each is replaced by its periodic
+// image, loaded by the threads once the copy has landed (the left seam has 8
+// such columns, the right one up to SCOL - 9 with Lx >= SCOL).  The columns
+// come in 16-byte groups (Lx and the staging window's start are multiples of
+// the group), every thread issues all of its loads before it stores any, and
+// ghost rows, constant in x, are already complete.
+template <typename T, typename ST>
+__device__ __forceinline__ void seam_fixup(const StepArgs<T>& P, const Smem<T, ST>& S, int x0,
+                                           int r0, unsigned g) {
+  constexpr int SCOL = Smem<T, ST>::SCOL;
+  constexpr int EPV = 16 / (int)sizeof(ST);  // values per 16-byte group
+  constexpr int MAXV = (RPI * 16 * (SCOL / EPV) + NT - 1) / NT;  // groups per thread, at most
+  const int Lx = P.Lx, Ly = P.Ly;
+  const int nl = x0 < 0 ? -x0 / EPV : 0;                  // left: groups [0, nl)
+  const int hs = (Lx - x0) / EPV;                          // right: groups [hs, SCOL / EPV)
+  const int n = nl + (hs < SCOL / EPV ? SCOL / EPV - hs : 0);
+  ST* base = S.stage + slot_of(g) * (RPI * 16 * SCOL);
+  const ST* fin = static_cast<const ST*>(P.fin);
+  uint4 v[MAXV];
+  int at[MAXV];
+#pragma unroll
+  for (int m = 0; m < MAXV; ++m) {
+    const int e = threadIdx.x + m * NT;
+    at[m] = -1;
+    if (e < RPI * 16 * n) {
+      const int r = e / (16 * n), rem = e - r * (16 * n), k = rem / n, jj = rem - k * n;
+      const int row = r0 + r;
+      if (!(P.walls && (row < 0 || row >= Ly))) {
+        const int j = (jj < nl ? jj : hs + (jj - nl)) * EPV;  // staging column
+        const int x = wrapi(x0 + j, Lx);
+        v[m] = __ldg(reinterpret_cast<const uint4*>(
+            fin + (long long)k * P.plane + (long long)wrapi(row, Ly) * Lx + x));
+        at[m] = (r * 16 + k) * SCOL + j;
+      }
+    }
   }
+#pragma unroll
+  for (int m = 0; m < MAXV; ++m)
+    if (at[m] >= 0) *reinterpret_cast<uint4*>(base + at[m]) = v[m];
+  fence_proxy_async();  // before later tensor copies into the slot
+  __syncthreads();
 }
 
 // P1 for one warp quadrant: the RPI staged rows of the batch in slot `sbase`,
 // advected rows to the f* ring at `fbase` (thread's plane and group).
 template <int SX, int SY, int ORDER, int LIM, typename T, typename ST>
-__device__ __forceinline__ void advect_batch(AdvState<T>& st, const VelConst<T>& vc,
+__device__ __forceinline__ void advect_batch(typename AdvSel<T>::State& st, const VelConst<T>& vc,
                                              const ST* sbase, T* fbase) {
+  constexpr int SCOL = scol_of<ST>();
+  if constexpr (sizeof(T) == 4) {
+    const VelPairs vp = vel_pairs<SX>(vc);
 #pragma unroll
-  for (int r = 0; r < RPI; ++r) {
-    T out[4];
-    advect_row<SX, SY, ORDER, LIM>(st, sbase + r * (16 * SCOL), vc, out);
-    T* dst = fbase + r * (16 * REG);
-    if constexpr (sizeof(T) == 4) {
-      *reinterpret_cast<float4*>(dst) = make_float4(out[0], out[1], out[2], out[3]);
-    } else {
+    for (int r = 0; r < RPI; ++r) {
+      float out[4];
+      advect_row2<SX, SY, ORDER, LIM>(st, sbase + r * (16 * SCOL), vp, out);
+      *reinterpret_cast<float4*>(fbase + r * FRS) = make_float4(out[0], out[1], out[2], out[3]);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < RPI; ++r) {
+      T out[4];
+      advect_row<SX, SY, ORDER, LIM>(st, sbase + r * (16 * SCOL), vc, out);
+      T* dst = fbase + r * FRS;
       reinterpret_cast<double2*>(dst)[0] = make_double2(out[0], out[1]);
       reinterpret_cast<double2*>(dst)[1] = make_double2(out[2], out[3]);
     }
@@ -297,7 +341,7 @@ __device__ __forceinline__ void advect_batch(AdvState<T>& st, const VelConst<T>&
 // WARM) ..  (rings indexed by (row - ys + 6) mod 8).  The tile of P4(i) leaves
 // by a tensor store issued by thread 0 at the start of iteration i + 1 (or
 // after the loop), after the barrier that ends P4(i).
-template <typename T, typename ST, int ORDER, int LIM, bool VEC, bool DIAG>
+template <typename T, typename ST, int ORDER, int LIM, bool VEC, bool DIAG, bool REGU>
 __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, ST>& S, int strip,
                                             int ys, int ye, const CUtensorMap* tm, unsigned& gb,
                                             unsigned& gi, double& dmass) {
@@ -311,26 +355,19 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
   const VelConst<T> vc = P.v[k];
   const int Lx = P.Lx, Ly = P.Ly;
 
-  // wrapped global columns of the staging groups (region column 0 is global
-  // column strip*TW - XOFF; the first staging column is region column -4)
-  __syncthreads();  // previous segment done with S.col and the rings
-  if (tid < SG) {
-    const int x = strip * TW - XOFF - 4 + 4 * tid;
-    S.col[tid] = VEC ? wrapi(x, Lx) : (tid == 0 ? x : 0);
-  }
-  __syncthreads();
+  __syncthreads();  // previous segment done with the rings
 
-  AdvState<T> st;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-    st.Fp[i] = st.Ryp[i] = st.Syp[i] = st.Z1[i] = st.Z2[i] = st.pend[i] = T(0);
+  typename AdvSel<T>::State st;
+  memset(&st, 0, sizeof(st));
 
-  const StageSlots<T, ST> slots(P, S, VEC);
-  // interior strips stage by tensor copies, the strips at the periodic x
-  // seam (and lattices without a tensor map) by per-thread copies
+  constexpr int SCOL = Smem<T, ST>::SCOL;
+  const StageSlots<T, ST> slots;
+  // first staging column (region column -4); the strips at the periodic x
+  // seam get their wrapped columns from seam_fixup
   const int x0 = strip * TW - XOFF - 4;
-  const bool tma = VEC && P.tma_in && x0 >= 0 && x0 + SCOL <= Lx;
-  const bool tstore = VEC && P.tma_out;
+  const bool seam = VEC && (x0 < 0 || x0 + SCOL > Lx);
+  const bool producer = tid == PRODUCER;
+  const bool tstore = P.tma_out;
   const int nit = WARM + (ye - ys + RPI - 1) / RPI;
   const unsigned g0 = gb;
 
@@ -342,42 +379,39 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
   const bool p3_on = tid < RPI * (REG - 2);
   const int r3 = tid / (REG - 2), c3 = 1 + tid - r3 * (REG - 2);
   const bool p4_on = tid < P4T;
-  const int r4 = tid / TW, o4 = tid - r4 * TW;  // output column o4 of the strip
+  const int r4 = lane >> 3, o4 = 8 * warp + (lane & 7);  // row, output column of the strip
   const int c4 = XOFF + o4, x4 = strip * TW + o4;
 
-  issue_batch<T, ST, VEC>(P, S, slots, tm, tma, x0, ys - 4, g0, gi);
+  // batches g0 and g0 + 1 before the loop; in iteration it, batch g0 + it + 1
+  // gets its ghost rows (and per-thread loads) and, in the collision phase,
+  // the producer issues the tensor copies of batch g0 + it + 2
+  ghost_rows<T, ST>(P, S, slots, ys - 4, g0);
+  if constexpr (VEC) {
+    if (producer) {
+      arm_tma<T, ST>(P, S, tm, x0, ys - 4, g0, gi);
+      if (nit > 1) arm_tma<T, ST>(P, S, tm, x0, ys, g0 + 1, gi);
+    }
+  } else {
+    load_scalar<T, ST>(P, S, slots, x0, ys - 4, g0, gi);
+  }
 
   T dseg = T(0);  // fused diagnostics: mass of this thread's nodes (rho - rho_ref)
   int nseg = 0;
   for (int it = 0; it < nit; ++it) {
     const unsigned gcur = g0 + (unsigned)it;
     const int B = ys - 4 + RPI * it;  // first staged row of this iteration
-    // ---------------- L: next batch, the previous iteration's output tile
-    if (it + 1 < nit) issue_batch<T, ST, VEC>(P, S, slots, tm, tma, x0, B + RPI, gcur + 1, gi);
-    else cp_async_commit();
-    if (tstore && tid == 0) {
-      bool stored = false;
-      if (it - 1 >= WARM) {
-        const int row0 = ys + RPI * (it - 1 - WARM);
-        const ST* tile = S.out + ((it - 1) & 1) * (RPI * 16 * TW);
-        if (row0 + RPI <= ye) {
-          tma_store_rows(tm + 2, strip * TW, row0, tile);
-        } else {
-          for (int r = 0; row0 + r < ye; ++r)
-            tma_store_rows(tm + 3, strip * TW, row0 + r, tile + r * 16 * TW);
-        }
-        bulk_commit();
-        stored = true;
-      }
-      // the tile P4 writes next was last stored two iterations ago
-      if (stored) bulk_wait_read<1>(); else bulk_wait_read<0>();
+    // ---------------- L: the next batch's ghost rows (and loads), wait for this one
+    if (it + 1 < nit) {
+      ghost_rows<T, ST>(P, S, slots, B + RPI, gcur + 1);
+      if constexpr (!VEC) load_scalar<T, ST>(P, S, slots, x0, B + RPI, gcur + 1, gi);
     }
-    wait_batch(P, S, gcur, tma);
+    wait_batch<VEC>(P, S, gcur);
+    if (seam) seam_fixup<T, ST>(P, S, x0, B, gcur);
 
     // ---------------- P1: advect the staged batch into f* rows B - 2 ..
     {
-      const ST* sb = p1_src + (gcur & 1u) * (RPI * 16 * SCOL);
-      T* fb = p1_dst + (it & 1) * (RPI * 16 * REG);
+      const ST* sb = p1_src + slot_of(gcur) * (RPI * 16 * SCOL);
+      T* fb = p1_dst + (it & 1) * (RPI * FRS);
       switch (q) {
         case 0: advect_batch<+1, +1, ORDER, LIM>(st, vc, sb, fb); break;
         case 1: advect_batch<-1, +1, ORDER, LIM>(st, vc, sb, fb); break;
@@ -391,7 +425,7 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
           const int a = B - 2 + r;
           if (a < 0 || a >= Ly) {
             const T gv = a < 0 ? vc.gbot : vc.gtop;
-            T* dst = fb + r * (16 * REG);
+            T* dst = fb + r * FRS;
 #pragma unroll
             for (int m = 0; m < 4; ++m) dst[m] = gv;
           }
@@ -400,10 +434,20 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
     }
     __syncthreads();
 
+    // the previous iteration's output tile leaves (its writes were fenced
+    // before the barrier that ended that iteration)
+    if (tstore && producer) {
+      const int row0 = ys + RPI * (it - 1 - WARM);  // rows of the previous iteration's P4
+      if (it - 1 >= WARM && row0 + RPI <= ye) {       // (a partial batch is stored per thread)
+        tma_store_rows(tm + 2, strip * TW, row0, S.out);
+        bulk_commit();
+      }
+    }
+
     // ---------------- P2: moments of rows B - 2 .., one thread per node
     if (it >= 1) {
       const int sl = (it & 1) * RPI + r2;
-      const T* src = S.fs + sl * (16 * REG) + c2;
+      const T* src = S.fs + sl * FRS + c2;
       T f[16];
 #pragma unroll
       for (int kk = 0; kk < 16; ++kk) f[kk] = src[kk * REG];
@@ -413,21 +457,36 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
 #pragma unroll
       for (int gg = 0; gg < 4; ++gg) {
         const T* fg = f + 4 * gg;
-        const T A = fg[0] - fg[2], Bm = fg[1] - fg[3];
+        T A, Bm, s02, s13;
+        if constexpr (sizeof(T) == 4) {  // (f0 +- f2, f1 +- f3) as packed pairs
+          const float2 a = make_float2(fg[0], fg[1]), b = make_float2(fg[2], fg[3]);
+          const float2 sp = add2(a, b), sm = sub2(a, b);
+          s02 = sp.x; s13 = sp.y; A = sm.x; Bm = sm.y;
+        } else {
+          s02 = fg[0] + fg[2]; s13 = fg[1] + fg[3]; A = fg[0] - fg[2]; Bm = fg[1] - fg[3];
+        }
         sx[gg] = A - Bm;
         sy[gg] = A + Bm;
-        d[gg] = (fg[0] + fg[2]) + (fg[1] + fg[3]);
+        d[gg] = s02 + s13;
       }
       const T dr = (d[0] + d[1]) + (d[2] + d[3]);
-      const T mx = P.xlo * (sx[0] + sx[2]) + P.xhi * (sx[1] + sx[3]);
-      const T my = P.xlo * (sy[0] + sy[1]) + P.xhi * (sy[2] + sy[3]);
       const T rho = P.rho_ref + dr;
       const T ir = rcp(rho);
-      const int m = sl * REG + c2;
+      const int m = sl * MP + c2;
       S.rho[m] = rho;
       S.drho[m] = dr;
-      S.ux[m] = mx * ir;
-      S.uy[m] = my * ir;
+      if constexpr (sizeof(T) == 4) {  // (rho ux, rho uy) and u as packed pairs
+        const float2 mlo = add2(make_float2(sx[0], sy[0]), make_float2(sx[2], sy[1]));
+        const float2 mhi = add2(make_float2(sx[1], sy[2]), make_float2(sx[3], sy[3]));
+        const float2 u = mul2(fma2(dup2(P.xlo), mlo, mul2(dup2(P.xhi), mhi)), dup2(ir));
+        S.ux[m] = u.x;
+        S.uy[m] = u.y;
+      } else {
+        const T mx = P.xlo * (sx[0] + sx[2]) + P.xhi * (sx[1] + sx[3]);
+        const T my = P.xlo * (sy[0] + sy[1]) + P.xhi * (sy[2] + sy[3]);
+        S.ux[m] = mx * ir;
+        S.uy[m] = my * ir;
+      }
       // p^i - p^w = rho T - [rho T/(1 - b rho) - a rho^2]   (Eqs. eder, evdw)
       const T rT = rho * P.Tt;
       S.phi[m] = fma(P.a * rho, rho, rT - rT * rcp(T(1) - P.b * rho));
@@ -437,13 +496,14 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
     // ---------------- P3: Laplacian of rho* on rows B - 3 ..
     if (it >= 1 && p3_on) {
       const int s0 = ((it & 1) * RPI + r3 + 7) & 7;  // row B - 3 + r3
-      const T* R0 = S.rho + s0 * REG + c3;
-      const T* Rm = S.rho + ((s0 + 7) & 7) * REG + c3;
-      const T* Rp = S.rho + ((s0 + 1) & 7) * REG + c3;
+      const T* R0 = S.rho + s0 * MP + c3;
+      const T* Rm = S.rho + ((s0 + 7) & 7) * MP + c3;
+      const T* Rp = S.rho + ((s0 + 1) & 7) * MP + c3;
       const T nn = (R0[-1] + R0[1]) + (Rm[0] + Rp[0]);
       const T dg = (Rm[-1] + Rm[1]) + (Rp[-1] + Rp[1]);
-      S.lap[s0 * REG + c3] = fma(P.lp1, nn, fma(P.lp2, dg, -P.lp0 * R0[0]));
+      S.lap[s0 * MP + c3] = fma(P.lp1, nn, fma(P.lp2, dg, -P.lp0 * R0[0]));
     }
+    if (tstore && producer) bulk_wait_read<0>();  // the tile is free for this P4
     __syncthreads();
 
     // ---------------- P4: g, collision of all planes, output tile (rows B - 4 ..)
@@ -452,11 +512,11 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
       T rho_post = T(-1);        // post-step density of this thread's node, if it has one
       if (c < ye && x4 < Lx) {
         const int s0 = ((it & 1) * RPI + r4 + 6) & 7;
-        const int sc = s0 * REG + c4;
-        const int sm = ((s0 + 7) & 7) * REG + c4;
-        const int sp = ((s0 + 1) & 7) * REG + c4;
-        const int s2m = ((s0 + 6) & 7) * REG + c4;
-        const int s2p = ((s0 + 2) & 7) * REG + c4;
+        const int sc = s0 * MP + c4;
+        const int sm = ((s0 + 7) & 7) * MP + c4;
+        const int sp = ((s0 + 1) & 7) * MP + c4;
+        const int s2m = ((s0 + 6) & 7) * MP + c4;
+        const int s2p = ((s0 + 2) & 7) * MP + c4;
         const T* ph = S.phi;
         const T* lp = S.lap;
         // fourth-order 5x5 gradient of p^i - p^w: the combination (4 D_h - D_2h)/3
@@ -489,11 +549,11 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
         const T mxg[2] = {lo * gdx, hi * gdx}, myg[2] = {lo * gdy, hi * gdy};
 
         T f[16];
-        const T* src = S.fs + s0 * (16 * REG) + c4;
+        const T* src = S.fs + s0 * FRS + c4;
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) f[kk] = src[kk * REG];
 
-        if (P.regularize) {
+        if constexpr (REGU) {
           // Eq. (ereg): replace f* by f^eq + w [H2:A2/2 + H3:A3/6], A_n = sum f^neq xi^n
           T m2xx = 0, m2xy = 0, m2yy = 0, m3xxx = 0, m3xxy = 0, m3xyy = 0, m3yyy = 0;
 #pragma unroll
@@ -534,6 +594,38 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
         // patterns s and s + 2) differ only in the sign of xi.u and xi.g: the
         // cubic splits into even and odd parts E and O, poly(+-) = E +- O
         T outv[16];
+        if constexpr (sizeof(T) == 4) {
+          // FP32: the two sign patterns (+,+), (-,+) of a group as one packed
+          // pair (their xi.u differ in the sign of the x term), the same
+          // operations per component as the scalar form below
+          const float2 rho2 = dup2(rho), p0_2 = dup2(p0), p1_2 = dup2(p1), p2_2 = dup2(p2);
+          const float2 ux2 = dup2(ux), uy2 = dup2(uy), gx2 = dup2(gdx), gy2 = dup2(gdy);
+          const float2 apm[2] = {mul2(make_float2(lo, -lo), ux2), mul2(make_float2(hi, -hi), ux2)};
+          const float2 bb[2] = {mul2(dup2(lo), uy2), mul2(dup2(hi), uy2)};
+          const float2 gpm[2] = {mul2(make_float2(lo, -lo), gx2), mul2(make_float2(hi, -hi), gx2)};
+          const float2 gb[2] = {mul2(dup2(lo), gy2), mul2(dup2(hi), gy2)};
+          const float2 s1 = dup2(P.one_m_omega), om2 = dup2(P.om2), om6 = dup2(P.om6);
+#pragma unroll
+          for (int grp = 0; grp < 4; ++grp) {
+            const ClassConst<T>& cl = P.cls[grp];
+            const int ix = grp & 1, iy = grp >> 1;
+            const float2 P0 = add2(p0_2, dup2(cl.omA)), P1 = add2(p1_2, dup2(cl.Ak));
+            const float2 K1c = add2(p2_2, dup2(cl.omB));
+            const float2 sw = mul2(dup2(cl.w), rho2), nsw = mul2(dup2(-cl.w), rho2);
+            const float2 cu = add2(bb[iy], apm[ix]);  // xi.u of (+,+), (-,+)
+            const float2 D = add2(gb[iy], gpm[ix]);   // dt xi.g
+            const float2 c2 = mul2(cu, cu);
+            const float2 E = fma2(c2, om2, fma2(cu, D, P0));
+            const float2 O = fma2(cu, fma2(c2, om6, K1c), mul2(D, fma2(c2, dup2(0.5f), P1)));
+            const float2 Q = mul2(sw, E);
+            const float2 op = fma2(s1, make_float2(f[4 * grp], f[4 * grp + 1]), fma2(sw, O, Q));
+            const float2 om = fma2(s1, make_float2(f[4 * grp + 2], f[4 * grp + 3]), fma2(nsw, O, Q));
+            outv[4 * grp] = op.x;
+            outv[4 * grp + 1] = op.y;
+            outv[4 * grp + 2] = om.x;
+            outv[4 * grp + 3] = om.y;
+          }
+        } else {
 #pragma unroll
         for (int grp = 0; grp < 4; ++grp) {
           const ClassConst<T>& cl = P.cls[grp];
@@ -556,6 +648,7 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
             outv[kk + 2] = fma(P.one_m_omega, f[kk + 2], fma(-sw, O, Q));
           }
         }
+        }
         rho_post = rho;  // the collision conserves mass
         if (P.reservoir) {
           // Sec. III A: outside R_BC the node is rescaled to rho_ext: f -> s f,
@@ -569,10 +662,10 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
               outv[kk] = fma(s, outv[kk], P.cls[kk >> 2].w * P.rho_ref * (s - T(1)));
           }
         }
-        if (tstore) {
-          ST* dst = S.out + ((it & 1) * RPI + r4) * (16 * TW) + o4;
+        if (tstore && B + RPI - 4 <= ye) {  // a full batch: the tile
+          ST* dst = S.out + r4 * TW + o4;
 #pragma unroll
-          for (int kk = 0; kk < 16; ++kk) dst[kk * TW] = to_store<ST, T>(outv[kk]);
+          for (int kk = 0; kk < 16; ++kk) dst[kk * (RPI * TW)] = to_store<ST, T>(outv[kk]);
         } else {
           ST* dst = static_cast<ST*>(P.fout) + (long long)c * Lx + x4;
           const long long pl = P.plane;
@@ -603,32 +696,48 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
         }
       }
     }
+    // the producer (no collision node) issues batch it + 2 meanwhile: its slot
+    // was last read by P1 of the previous iteration
+    if constexpr (VEC) {
+      if (producer && it + 2 < nit) arm_tma<T, ST>(P, S, tm, x0, B + 2 * RPI, gcur + 2, gi);
+    }
     if (tstore) fence_proxy_async();  // the tile's generic writes before its tensor store
     __syncthreads();
   }
   // the last tile of the segment
-  if (tstore && tid == 0) {
-    const int it = nit - 1;
-    const int row0 = ys + RPI * (it - WARM);
-    const ST* tile = S.out + (it & 1) * (RPI * 16 * TW);
+  if (tstore && producer) {
+    const int row0 = ys + RPI * (nit - 1 - WARM);
     if (row0 + RPI <= ye) {
-      tma_store_rows(tm + 2, strip * TW, row0, tile);
-    } else {
-      for (int r = 0; row0 + r < ye; ++r)
-        tma_store_rows(tm + 3, strip * TW, row0 + r, tile + r * 16 * TW);
+      tma_store_rows(tm + 2, strip * TW, row0, S.out);
+      bulk_commit();
     }
-    bulk_commit();
   }
-  cp_async_wait<0>();
   gb = g0 + (unsigned)nit;
   if (DIAG) dmass += (double)dseg + (double)P.rho_ref * (double)nseg;
 }
 
-// Work items are (row block, strip) pairs in row-block-major order, claimed
-// from a device counter: CTAs that run at the same time work on the same rows
-// of neighbouring strips, so the halo columns they share and the output lines
-// they both write meet in L2.  The last CTA to finish resets the counters, so
-// the next launch (or a replay of a captured graph) starts from zero.
+// Work items are (row block, strip) pairs claimed from a device counter: first
+// the strips at the periodic x seam (slower: they complete their staging
+// window by hand), so that they do not end up as the launch's tail, then the
+// others in row-block-major order, so that CTAs running at the same time work
+// on the same rows of neighbouring strips and the halo columns they share and
+// the output lines they both write meet in L2.  The last CTA to finish resets
+// the counters, so the next launch (or a replay of a captured graph) starts
+// from zero.
+__device__ __forceinline__ void item_coords(long long item, int nstrip, long long nrb, int& strip,
+                                            long long& rb) {
+  if (nstrip < 3) {
+    rb = item / nstrip;
+    strip = (int)(item - rb * nstrip);
+  } else if (item < 2 * nrb) {
+    rb = item >> 1;
+    strip = (item & 1) ? nstrip - 1 : 0;
+  } else {
+    const long long j = item - 2 * nrb;
+    rb = j / (nstrip - 2);
+    strip = 1 + (int)(j - rb * (nstrip - 2));
+  }
+}
 __device__ __forceinline__ long long claim_item(unsigned long long* sched, long long* s_item) {
   __syncthreads();  // everyone has read the previous item
   if (threadIdx.x == 0) *s_item = (long long)atomicAdd(&sched[0], 1ULL);
@@ -648,17 +757,17 @@ __device__ __forceinline__ void retire_cta(unsigned long long* sched) {
 // Before the CTA leaves: every tensor store has completed, and every staged
 // batch it armed has landed.  Normally all were waited for; after a timed-out
 // wait (abort = first such batch + 1) the batches from that one up to the
-// last armed may still be in flight into this CTA's shared memory, and thread
-// 0 waits for each again, bounded, so that no copy outlives the CTA unless
-// the copy engine itself is stuck.
+// last armed may still be in flight into this CTA's shared memory, and the
+// producer waits for each again, bounded, so that no copy outlives the CTA
+// unless the copy engine itself is stuck.
 template <typename SM>
 __device__ __forceinline__ void drain_copies(const SM& S, unsigned armed) {
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == PRODUCER) {
     bulk_wait_all();
     const int a = *reinterpret_cast<volatile int*>(S.abort);
     if (a > 0)
       for (unsigned b = (unsigned)(a - 1); b < armed; ++b)
-        mbar_wait_bounded(S.bar + (b & 1u), (b >> 1) & 1u, 2000000000ULL);
+        mbar_wait_bounded(S.bar + slot_of(b), parity_of(b), 2000000000ULL);
   }
 }
 
@@ -667,16 +776,16 @@ __device__ __forceinline__ void init_cta_barriers(unsigned long long* dsums,
   if (threadIdx.x == 0) {
     for (int t = 0; t < 6; ++t) dsums[t] = 0ULL;
     *abort = 0;
-    mbar_init(bar, 1);
-    mbar_init(bar + 1, 1);
+    for (int b = 0; b < NSLOT; ++b) mbar_init(bar + b, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
 }
 
 // DIAG: fuse the diagnostics of the state after the step (P.diag_mass and
-// P.diag_sums receive them); a separate instantiation so that the plain step
-// executes none of their instructions.
-template <typename T, typename ST, int ORDER, int LIM, bool VEC, bool DIAG>
+// P.diag_sums receive them); REGU: the regularised collision (Eq. ereg).  Both
+// are separate instantiations, so that the plain step carries none of their
+// instructions (cold code in the loop body costs instruction fetch).
+template <typename T, typename ST, int ORDER, int LIM, bool VEC, bool DIAG, bool REGU>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     step_kernel(const __grid_constant__ StepArgs<T> P, const __grid_constant__ RowMaps maps) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -684,17 +793,18 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
   __shared__ long long s_item;
   init_cta_barriers(S.dsums, S.bar, S.abort);
   const CUtensorMap* tm = maps.m;
-  unsigned gb = 0;     // staged batches of this CTA so far (ring slot g & 1, phase (g >> 1) & 1)
-  unsigned gi = 0;     // thread 0: batches armed on the mbarriers
+  unsigned gb = 0;     // staged batches of this CTA so far (slot g % NSLOT)
+  unsigned gi = 0;     // the producer: batches armed on the mbarriers
   double dmass = 0.0;  // fused diagnostics: this thread's mass over all its segments
   for (;;) {
     const long long item = claim_item(P.sched, &s_item);
     if (item >= P.items) break;
-    const long long rb = item / P.nstrip;
-    const int strip = (int)(item - rb * P.nstrip);
+    int strip;
+    long long rb;
+    item_coords(item, P.nstrip, P.items / P.nstrip, strip, rb);
     const int ys = (int)(rb * P.row_block);
     const int ye = min(P.Ly, ys + P.row_block);
-    run_segment<T, ST, ORDER, LIM, VEC, DIAG>(P, S, strip, ys, ye, tm, gb, gi, dmass);
+    run_segment<T, ST, ORDER, LIM, VEC, DIAG, REGU>(P, S, strip, ys, ye, tm, gb, gi, dmass);
   }
   if (DIAG) {
     // one warp sum and one global add per warp for the mass; claim_item's
@@ -711,7 +821,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
 
 // Several lattices advanced by one launch: their work items are concatenated
 // and claimed from one counter; each lattice brings its own tensor maps.
-template <typename T, int ORDER, int LIM, bool VEC>
+template <typename T, int ORDER, int LIM, bool VEC, bool REGU>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     step_batch_kernel(const __grid_constant__ BatchArgs<T> B) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -727,11 +837,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     while (B.item_start[i + 1] <= item) ++i;
     const StepArgs<T>& P = B.L[i];
     const long long local = item - B.item_start[i];
-    const long long rb = local / P.nstrip;
-    const int strip = (int)(local - rb * P.nstrip);
+    int strip;
+    long long rb;
+    item_coords(local, P.nstrip, P.items / P.nstrip, strip, rb);
     const int ys = (int)(rb * P.row_block);
     const int ye = min(P.Ly, ys + P.row_block);
-    run_segment<T, T, ORDER, LIM, VEC, false>(P, S, strip, ys, ye, B.maps[i].m, gb, gi, dmass);
+    run_segment<T, T, ORDER, LIM, VEC, false, REGU>(P, S, strip, ys, ye, B.maps[i].m, gb, gi, dmass);
   }
   drain_copies(S, gi);
   retire_cta(B.sched);

@@ -83,3 +83,41 @@ def test_server_diagnostics_schedule_and_poll():
             big = S.Job(params=P.Params(Lx=4096, Ly=4096), rho=np.ones((4096, 4096)),
                         ux=np.zeros((4096, 4096)), uy=np.zeros((4096, 4096)), nsteps=1)
             srv.submit(big)
+
+
+def test_server_large_jobs_equal_alone_in_the_mix():
+    """Jobs of 512^2 .. 1024^2 nodes and 1000 .. 1200 steps, overlapping in the
+    server's batched launches (graph launches of 16 steps), each ends where it
+    ends alone through lbm_step: the batched kernel runs every node through
+    the same arithmetic, so FP32 results agree to rounding (the bar is the
+    FP32 accuracy bar, 1e-5; the difference measured is printed) and the FP64
+    job, which steps on its own, agrees bit for bit."""
+    import torch
+    import paper_1802_01272_gb300 as P
+    from paper_1802_01272_gb300 import server as S
+    stream = torch.cuda.current_stream()
+    spec = [(512, 1000, P.LBM_FP32_SHIFTED), (768, 1200, P.LBM_FP32_SHIFTED),
+            (1024, 1000, P.LBM_FP32_SHIFTED), (512, 1100, P.LBM_FP32_SHIFTED),
+            (512, 1000, P.LBM_FP64)]
+    jobs = []
+    for i, (L, n, prec) in enumerate(spec):
+        lp = P.Params(Lx=L, Ly=L, T=0.85, tau=1e-3, rho_ext=1.6, rho_ref=1.6, precision=prec)
+        rho, ux, uy = synth.bubble(L, L, 1.6, 0.5, R=L / 8, W=3)
+        jobs.append(S.Job(params=lp, rho=rho, ux=ux, uy=uy, nsteps=n, arrival=0.01 * i,
+                          diag_threshold=1.0, keep_rho=True))
+    with S.BatchServer(int(16e9), chunk=400) as srv:
+        S.run_jobs(srv, jobs)
+        info = srv.info()
+    assert info["done"] == len(jobs) and info["failed"] == 0
+    for j in jobs:
+        with P.Lattice(j.params, stream) as L:
+            L.init_rho_u(j.rho, j.ux, j.uy)
+            L.step(j.nsteps)
+            r, _, _ = L.moments()
+        err = float(np.abs(r - j.rho_out).max() / np.abs(r).max())
+        print(f"\n{j.params.Lx}^2 x {j.nsteps} steps, precision {j.params.precision}: "
+              f"alone vs in the mix {err:.3e}")
+        if j.params.precision == P.LBM_FP64:
+            assert np.array_equal(r, j.rho_out)
+        else:
+            assert err < 1e-5

@@ -24,8 +24,13 @@ committed capture, against the peaks the library measures on the device with
 lbm_measure_peaks), `e2e` (the same metric through the C ABI with pinned host
 buffers, copies inside the timed region; median of five runs, with its phase
 times), `cpu_baseline` (the FP64 oracle on
-the host cores and on one thread), `clocks`, and `config.launch` (the launch
-geometry lbm_tune chose before the warm-up, or --row-block's).
+the host cores and on one thread), `clocks`, `config.launch` (the launch
+geometry lbm_tune chose before the warm-up, or --row-block's), `runs` (five
+more device-resident regions of >= 1 s: GLUPS of each, median, spread) and
+`server` (--server NJOBS, default 24: the sweep-server job mix through the
+native batch server against the same jobs one at a time -- capacity with every
+job submitted at once, then p50/p99 latency and throughput under Poisson
+arrivals at twice the serial capacity).
 """
 from __future__ import annotations
 
@@ -107,6 +112,8 @@ def kernel_source_hash():
 
 E2E_REPS = 5  # repetitions of the end-to-end region (median reported)
 RUNS, RUN_S = 5, 1.0  # repeated device-resident regions (median and spread reported)
+SERVER_LOAD = 2.0      # offered load of the server comparison, x the serial capacity
+U_WALL_MAX = 0.5       # server jobs: wall speed cap (Mach ~0.3 in the liquid)
 
 
 def ncu_record(workload):
@@ -218,8 +225,10 @@ def cpu_baseline_single_thread(workload, seconds=5.0):
 def server_jobs(P, S, njobs, step_scale, seed=4, rate_hz=None):
     """Config 5's job mix: lattices L^2, L in {256, 512, 1024, 2048}; T ~ U[0.75, 0.98];
     shear rate from Ca ~ U[0, 0.4] (Ca = mu_L gamma_dot R / sigma with the seed
-    radius R, mu_L = rho_L T tau); a tanh vapour seed (R = 20, W = 4) in liquid at
-    rho_L(T); steps ~ U{5000..20000} x step_scale; Poisson arrivals."""
+    radius R, mu_L = rho_L T tau), with the wall speed u_w = gamma_dot L ds / 2
+    capped at U_WALL_MAX (on the large lattices Ca = 0.4 at R = 20 nodes would
+    need walls faster than sound); a tanh vapour seed (R = 20, W = 4) in liquid
+    at rho_L(T); steps ~ U{5000..20000} x step_scale; Poisson arrivals."""
     import numpy as np
     import synth
     from paper_1802_01272_gb300 import eos
@@ -232,7 +241,7 @@ def server_jobs(P, S, njobs, step_scale, seed=4, rate_hz=None):
         rl, rv = eos.coexistence(T)
         sigma = eos.interface_tension(T, 1e-4)
         tau = 1e-2
-        gdot = ca * sigma / (rl * T * tau * 20 * DS)
+        gdot = min(ca * sigma / (rl * T * tau * 20 * DS), 2.0 * U_WALL_MAX / (L * DS))
         p = P.Params(Lx=L, Ly=L, T=T, tau=tau, dt=DT, ds=DS, rho_ext=rl, rho_ref=rl,
                      boundary=P.LBM_BC_SHEAR_WALLS if gdot > 0 else P.LBM_BC_PERIODIC,
                      shear_rate=gdot)
@@ -247,22 +256,25 @@ def server_jobs(P, S, njobs, step_scale, seed=4, rate_hz=None):
 
 
 def run_server_bench(P, stream, njobs, step_scale):
-    """Continuous batching vs the same jobs one at a time (same GPU, same jobs)."""
+    """Continuous batching vs the same jobs one at a time (same GPU, same jobs).
+    Capacity: every job submitted at t = 0 (GLUPS = work / makespan).  Then
+    Poisson arrivals offered at LOAD x the serial capacity, for the latencies
+    (p50, p99 of finish - arrival) and the throughput under that load."""
     from paper_1802_01272_gb300 import server as S
     jobs = server_jobs(P, S, njobs, step_scale)
     work = sum(j.node_updates for j in jobs)
-    # offered load ~1.2x of the serial throughput, measured on the first job
-    probe = server_jobs(P, S, 1, step_scale)[0]
-    t0 = time.perf_counter()
-    S.run_serial([probe], stream)
-    rate = probe.node_updates / (time.perf_counter() - t0)
-    mean_work = work / njobs
-    jobs = server_jobs(P, S, njobs, step_scale, rate_hz=1.2 * rate / mean_work)
-    serial_jobs = server_jobs(P, S, njobs, step_scale, rate_hz=1.2 * rate / mean_work)
+    cap_serial = S.run_serial(server_jobs(P, S, njobs, step_scale), stream)
+    with S.BatchServer(mem_budget_bytes=int(64e9), chunk=100) as srv:
+        cap_batched = S.run_jobs(srv, server_jobs(P, S, njobs, step_scale))
+    rate_hz = SERVER_LOAD * cap_serial.glups * 1e9 / (work / njobs)
+    jobs = server_jobs(P, S, njobs, step_scale, rate_hz=rate_hz)
     with S.BatchServer(mem_budget_bytes=int(64e9), chunk=100) as srv:
         st = S.run_jobs(srv, jobs)
-    ss = S.run_serial(serial_jobs, stream)
+    ss = S.run_serial(server_jobs(P, S, njobs, step_scale, rate_hz=rate_hz), stream)
     return {"jobs": njobs, "steps_scale": step_scale, "node_updates": work,
+            "capacity_glups": {"batched": cap_batched.glups, "serial": cap_serial.glups,
+                               "note": "all jobs submitted at t = 0; work / makespan"},
+            "offered_load": f"Poisson arrivals at {SERVER_LOAD} x the serial capacity",
             "batched": {"glups": st.glups, "p50_s": st.pct(50), "p99_s": st.pct(99),
                         "makespan_s": st.makespan, "launches": st.launches,
                         "server": "native lbm_batch_* (C++ worker thread)"},
@@ -410,7 +422,7 @@ def main():
     ms = max_over_ranks(ms)
     ms_per_step = ms / args.steps
     value = world * nodes * args.steps / (ms * 1e-3) / 1e9
-    runs = [world * nodes * rep_steps / (m * 1e-3) / 1e9 for m in run_ms]
+    rep_glups = [world * nodes * rep_steps / (m * 1e-3) / 1e9 for m in run_ms]
 
     # roofline of the step kernel: the only kernel in the timed region
     peak, peak_kind = load_peaks()
@@ -519,9 +531,10 @@ def main():
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                          if peak_kind == "measured" else "fallback 6.8 TB/s",
                          "algorithmic_bytes_per_launch": alg_bytes},
-            "runs": {"steps_each": rep_steps, "glups": runs,
-                     "median": statistics.median(runs) if runs else None,
-                     "spread": (max(runs) - min(runs)) / statistics.median(runs) if runs else None},
+            "runs": {"steps_each": rep_steps, "glups": rep_glups,
+                     "median": statistics.median(rep_glups) if rep_glups else None,
+                     "spread": (max(rep_glups) - min(rep_glups)) / statistics.median(rep_glups)
+                     if rep_glups else None},
             "issue_roofline": issue_roof,
             "fp32_roofline": fp32_roof,
             "gpu_launches": args.steps,

@@ -184,11 +184,15 @@ void fill_step_args(lbm_handle* h, StepArgs<T>& a) {
   a.gw2 = (T)(1.0 / 9.0 * lam);
   a.gw3 = (T)(1.0 / 18.0 * lam);
   a.gw4 = (T)(1.0 / 72.0 * lam);
-  a.lw1 = (T)(1.0 / 3.0 * p.kappa * lam);
-  a.lw2 = (T)(1.0 / 12.0 * p.kappa * lam);
-  a.lp1 = (T)(2.0 / 3.0 / (p.ds * p.ds));
-  a.lp2 = (T)(1.0 / 6.0 / (p.ds * p.ds));
-  a.lp0 = (T)(10.0 / 3.0 / (p.ds * p.ds));
+  // D_h (weights 1/3 axial, 1/12 diagonal) applied to the 9-point Laplacian
+  // (2/3, 1/6, -10/3) / ds^2 is the 5x5 stencil W(a, b) = -W(-a, b) =
+  // W(a, -b) with W(1, 0) = -1, W(1, 1) = -1/18, W(1, 2) = 1/18, W(2, 0) = 1/4,
+  // W(2, 1) = 1/9, W(2, 2) = 1/72 (units 1/ds^3; W(0, b) = 0)
+  {
+    const double kl = p.kappa * lam / (p.ds * p.ds);
+    const double w[6] = {-1.0, -1.0 / 18.0, 1.0 / 18.0, 0.25, 1.0 / 9.0, 1.0 / 72.0};
+    for (int i = 0; i < 6; ++i) a.kw[i] = (T)(w[i] * kl);
+  }
   a.omega = (T)om;
   a.one_m_omega = (T)(1.0 - om);
   a.om2 = (T)(0.5 * om);

@@ -285,7 +285,7 @@ cudaError_t launch_hist(const AuxArgs& a, const void* f, int nbins, double lo, d
 }
 
 size_t step_smem_bytes(size_t stage_elem, size_t elem) {
-  const size_t elems = (size_t)FROWS * FRS + 6 * (size_t)MROWS * MP;
+  const size_t elems = (size_t)FROWS * FRS + 4 * (size_t)MROWS * MP;  // f*, drho, ux, uy, phi
   // + 128 bytes to align the staging ring and the output tile for tensor
   // copies; the fused diagnostics' bubble-site sums, the staging slots'
   // mbarriers and the CTA's wait-abort flag

@@ -104,8 +104,10 @@ struct StepArgs {
   // force stencils with dt/ds (and kappa) folded in: g dt/ds = ir * (gradient
   // of p^i - p^w) + kappa * (gradient of the Laplacian)
   T gw1, gw2, gw3, gw4;     // (4/9, 1/9, 1/18, 1/72) dt/ds
-  T lw1, lw2;               // (1/3, 1/12) kappa dt/ds
-  T lp1, lp2, lp0;          // 9-point Laplacian: (2/3, 1/6, 10/3) / ds^2
+  // kappa D_h(9-point Laplacian) composed into one 5x5 stencil: weights of
+  // q(+-1, b) - q(-+1, b) for |b| = 0, 1, 2 and of q(+-2, b) - q(-+2, b),
+  // (-1, -1/18, 1/18, 1/4, 1/9, 1/72) kappa dt/ds^3
+  T kw[6];
   T rho_ext, rbc2, cxc, cyc;
   unsigned int* err;         // bit 0: non-finite or non-positive rho; bit 1: a wait timed out
   int tma_in;               // the tensor maps describe fin (interior strips stage by tensor copies)
@@ -399,6 +401,24 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
   return *reinterpret_cast<const float2*>(&r);
 }
 __device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+// the same pair operations on FP64 pairs, component by component
+__device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 sub2(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 mul2(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 dup2(double v) { return make_double2(v, v); }
+template <typename T>
+struct PairOf {
+  using type = float2;
+  static __device__ __forceinline__ float2 make(float a, float b) { return make_float2(a, b); }
+};
+template <>
+struct PairOf<double> {
+  using type = double2;
+  static __device__ __forceinline__ double2 make(double a, double b) { return make_double2(a, b); }
+};
 
 // the MC half-limited jump with h = (R + Ru)/4 given (see half_limited)
 template <int LIM>

@@ -91,12 +91,10 @@ struct Smem {
   ST* stage;  // [NSLOT][RPI][16][SCOL] f^n rows of the strip, with the advection halo
   ST* out;    // [16][RPI][TW] the f^{n+1} tile of the tensor store (plane-major)
   T* fs;      // [FROWS][FRS] advected f*: 16 planes of REG per row, padded
-  T* rho;     // [MROWS][MP]
-  T* drho;    // rho* - rho_ref
+  T* drho;    // [MROWS][MP] rho* - rho_ref
   T* ux;
   T* uy;
   T* phi;     // p^i - p^w
-  T* lap;     // 9-point Laplacian of rho*
   unsigned long long* dsums;  // [6] fused diagnostics: per-CTA bubble-site sums
   unsigned long long* bar;    // [NSLOT] mbarriers of the staging slots
   int* abort;                 // a bounded wait of this CTA timed out: stop waiting
@@ -108,13 +106,11 @@ struct Smem {
     T* p = reinterpret_cast<T*>(out + RPI * 16 * TW);
     fs = p;
     p += FROWS * FRS;
-    rho = p;
-    drho = rho + MROWS * MP;
+    drho = p;
     ux = drho + MROWS * MP;
     uy = ux + MROWS * MP;
     phi = uy + MROWS * MP;
-    lap = phi + MROWS * MP;
-    dsums = reinterpret_cast<unsigned long long*>(lap + MROWS * MP);  // 8-byte aligned
+    dsums = reinterpret_cast<unsigned long long*>(phi + MROWS * MP);  // 8-byte aligned
     bar = dsums + 6;
     abort = reinterpret_cast<int*>(bar + NSLOT);
   }
@@ -331,14 +327,51 @@ __device__ __forceinline__ void advect_batch(typename AdvSel<T>::State& st, cons
   }
 }
 
+// dt g / ds at one node (Eq. eder) from the moment rings; R[b + 2] is the ring
+// offset (column included) of the node's row + b, b = -2 .. 2.
+//  * grad(p^i - p^w): the fourth-order 5x5 gradient, the combination
+//    (4 D_h - D_2h)/3 of the isotropic 3x3 gradient D_h at spacings ds and 2 ds;
+//  * kappa grad(lap rho*): D_h of the isotropic 9-point Laplacian, the two
+//    composed into one 5x5 stencil and applied to rho* - rho_ref (the
+//    Laplacian of a constant vanishes), so no Laplacian row is kept.
+// The y components read the x stencils transposed: each (x, y) pair of
+// differences is one pair operation (packed FP32x2 in FP32).
+template <typename T>
+__device__ __forceinline__ void force_dt(const StepArgs<T>& P, const T* ph, const T* dq,
+                                         const int (&R)[5], T ir, T& gdx, T& gdy) {
+  using V = typename PairOf<T>::type;
+  auto PH = [&](int a, int b) { return ph[R[b + 2] + a]; };
+  auto Q = [&](int a, int b) { return dq[R[b + 2] + a]; };
+  // x: F(a, b) - F(-a, b); y: F(b, a) - F(b, -a)
+  auto dPH = [&](int a, int b) {
+    return sub2(PairOf<T>::make(PH(a, b), PH(b, a)), PairOf<T>::make(PH(-a, b), PH(b, -a)));
+  };
+  auto dQ = [&](int a, int b) {
+    return sub2(PairOf<T>::make(Q(a, b), Q(b, a)), PairOf<T>::make(Q(-a, b), Q(b, -a)));
+  };
+  const V t1 = dPH(1, 0), t2 = add2(dPH(1, 1), dPH(1, -1));
+  const V t3 = dPH(2, 0), t4 = add2(dPH(2, 2), dPH(2, -2));
+  const V pg = fma2(dup2(P.gw1), t1,
+                    fma2(dup2(P.gw2), t2, fma2(dup2(-P.gw3), t3, mul2(dup2(-P.gw4), t4))));
+  const V u0 = dQ(1, 0), u1 = add2(dQ(1, 1), dQ(1, -1)), u2 = add2(dQ(1, 2), dQ(1, -2));
+  const V v0 = dQ(2, 0), v1 = add2(dQ(2, 1), dQ(2, -1)), v2 = add2(dQ(2, 2), dQ(2, -2));
+  const V lg = fma2(dup2(P.kw[0]), u0,
+               fma2(dup2(P.kw[1]), u1,
+               fma2(dup2(P.kw[2]), u2,
+               fma2(dup2(P.kw[3]), v0, fma2(dup2(P.kw[4]), v1, mul2(dup2(P.kw[5]), v2))))));
+  const V g = fma2(dup2(ir), pg, lg);
+  gdx = g.x;
+  gdy = g.y;
+}
+
 // One row segment [ys, ye) of one strip of one lattice.  Every node's update
 // uses the same arithmetic in the same order whatever the segment boundaries,
 // so results do not depend on how the rows are split over CTAs or lattices.
 //
 // Iteration i consumes staged batch B_i = ys - 4 + 4 i .. +3 and, in the same
-// iteration, P1 writes f* of rows B_i - 2 .., P2 their moments, P3 the
-// Laplacian of rows B_i - 3 .., P4 the outputs of rows B_i - 4 .. = ys + 4 (i -
-// WARM) ..  (rings indexed by (row - ys + 6) mod 8).  The tile of P4(i) leaves
+// iteration, P1 writes f* of rows B_i - 2 .., P2 their moments, P4 the outputs
+// of rows B_i - 4 .. = ys + 4 (i - WARM) ..  (rings indexed by (row - ys + 6)
+// mod 8); three CTA barriers per iteration.  The tile of P4(i) leaves
 // by a tensor store issued by thread 0 at the start of iteration i + 1 (or
 // after the loop), after the barrier that ends P4(i).
 template <typename T, typename ST, int ORDER, int LIM, bool VEC, bool DIAG, bool REGU>
@@ -372,12 +405,10 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
   const unsigned g0 = gb;
 
   // per-thread bases: P1 (plane k, group g), P2 (node row r2, column c2),
-  // P3 (row r3, column c3), P4 (row r4, output column)
+  // P4 (row r4, output column)
   const ST* p1_src = S.stage + k * SCOL + 4 * g + 4;
   T* p1_dst = S.fs + k * REG + 4 * g;
   const int r2 = tid >> 6, c2 = tid & 63;
-  const bool p3_on = tid < RPI * (REG - 2);
-  const int r3 = tid / (REG - 2), c3 = 1 + tid - r3 * (REG - 2);
   const bool p4_on = tid < P4T;
   const int r4 = lane >> 3, o4 = 8 * warp + (lane & 7);  // row, output column of the strip
   const int c4 = XOFF + o4, x4 = strip * TW + o4;
@@ -400,7 +431,16 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
   for (int it = 0; it < nit; ++it) {
     const unsigned gcur = g0 + (unsigned)it;
     const int B = ys - 4 + RPI * it;  // first staged row of this iteration
-    // ---------------- L: the next batch's ghost rows (and loads), wait for this one
+    // ---------------- L: the previous iteration's output tile leaves (its
+    // writes were fenced before the barrier that ended that iteration); the
+    // next batch's ghost rows (and loads); wait for this batch
+    if (tstore && producer) {
+      const int row0 = ys + RPI * (it - 1 - WARM);  // rows of the previous iteration's P4
+      if (it - 1 >= WARM && row0 + RPI <= ye) {       // (a partial batch is stored per thread)
+        tma_store_rows(tm + 2, strip * TW, row0, S.out);
+        bulk_commit();
+      }
+    }
     if (it + 1 < nit) {
       ghost_rows<T, ST>(P, S, slots, B + RPI, gcur + 1);
       if constexpr (!VEC) load_scalar<T, ST>(P, S, slots, x0, B + RPI, gcur + 1, gi);
@@ -434,16 +474,6 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
     }
     __syncthreads();
 
-    // the previous iteration's output tile leaves (its writes were fenced
-    // before the barrier that ended that iteration)
-    if (tstore && producer) {
-      const int row0 = ys + RPI * (it - 1 - WARM);  // rows of the previous iteration's P4
-      if (it - 1 >= WARM && row0 + RPI <= ye) {       // (a partial batch is stored per thread)
-        tma_store_rows(tm + 2, strip * TW, row0, S.out);
-        bulk_commit();
-      }
-    }
-
     // ---------------- P2: moments of rows B - 2 .., one thread per node
     if (it >= 1) {
       const int sl = (it & 1) * RPI + r2;
@@ -473,7 +503,6 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
       const T rho = P.rho_ref + dr;
       const T ir = rcp(rho);
       const int m = sl * MP + c2;
-      S.rho[m] = rho;
       S.drho[m] = dr;
       if constexpr (sizeof(T) == 4) {  // (rho ux, rho uy) and u as packed pairs
         const float2 mlo = add2(make_float2(sx[0], sy[0]), make_float2(sx[2], sy[1]));
@@ -491,18 +520,6 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
       const T rT = rho * P.Tt;
       S.phi[m] = fma(P.a * rho, rho, rT - rT * rcp(T(1) - P.b * rho));
     }
-    __syncthreads();
-
-    // ---------------- P3: Laplacian of rho* on rows B - 3 ..
-    if (it >= 1 && p3_on) {
-      const int s0 = ((it & 1) * RPI + r3 + 7) & 7;  // row B - 3 + r3
-      const T* R0 = S.rho + s0 * MP + c3;
-      const T* Rm = S.rho + ((s0 + 7) & 7) * MP + c3;
-      const T* Rp = S.rho + ((s0 + 1) & 7) * MP + c3;
-      const T nn = (R0[-1] + R0[1]) + (Rm[0] + Rp[0]);
-      const T dg = (Rm[-1] + Rm[1]) + (Rp[-1] + Rp[1]);
-      S.lap[s0 * MP + c3] = fma(P.lp1, nn, fma(P.lp2, dg, -P.lp0 * R0[0]));
-    }
     if (tstore && producer) bulk_wait_read<0>();  // the tile is free for this P4
     __syncthreads();
 
@@ -517,27 +534,12 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
         const int sp = ((s0 + 1) & 7) * MP + c4;
         const int s2m = ((s0 + 6) & 7) * MP + c4;
         const int s2p = ((s0 + 2) & 7) * MP + c4;
-        const T* ph = S.phi;
-        const T* lp = S.lap;
-        // fourth-order 5x5 gradient of p^i - p^w: the combination (4 D_h - D_2h)/3
-        // of the isotropic 3x3 gradient D_h at spacings ds and 2 ds (times dt/ds)
-        const T px = P.gw1 * (ph[sc + 1] - ph[sc - 1]) +
-                     P.gw2 * ((ph[sp + 1] - ph[sp - 1]) + (ph[sm + 1] - ph[sm - 1])) -
-                     P.gw3 * (ph[sc + 2] - ph[sc - 2]) -
-                     P.gw4 * ((ph[s2p + 2] - ph[s2p - 2]) + (ph[s2m + 2] - ph[s2m - 2]));
-        const T py = P.gw1 * (ph[sp] - ph[sm]) +
-                     P.gw2 * ((ph[sp + 1] - ph[sm + 1]) + (ph[sp - 1] - ph[sm - 1])) -
-                     P.gw3 * (ph[s2p] - ph[s2m]) -
-                     P.gw4 * ((ph[s2p + 2] - ph[s2m + 2]) + (ph[s2p - 2] - ph[s2m - 2]));
-        // isotropic 3x3 gradient of the Laplacian (times kappa dt/ds)
-        const T lx = P.lw1 * (lp[sc + 1] - lp[sc - 1]) +
-                     P.lw2 * ((lp[sp + 1] - lp[sp - 1]) + (lp[sm + 1] - lp[sm - 1]));
-        const T ly = P.lw1 * (lp[sp] - lp[sm]) +
-                     P.lw2 * ((lp[sp + 1] - lp[sm + 1]) + (lp[sp - 1] - lp[sm - 1]));
-        const T rho = S.rho[sc], ux = S.ux[sc], uy = S.uy[sc], drho = S.drho[sc];
+        const int R[5] = {s2m, sm, sc, sp, s2p};
+        const T drho = S.drho[sc], ux = S.ux[sc], uy = S.uy[sc];
+        const T rho = P.rho_ref + drho;  // as in P2
         const T ir = rcp(rho);
-        const T gdx = fma(ir, px, lx);  // dt xi.g components: dt g
-        const T gdy = fma(ir, py, ly);
+        T gdx, gdy;  // dt xi.g components: dt g
+        force_dt<T>(P, S.phi, S.drho, R, ir, gdx, gdy);
         if (!(rho > T(0)) || !(rho < T(1e30))) atomicOr(P.err, 1u);
         const T e = T(1) - T(0.5) * (ux * ux + uy * uy);
         const T h = gdx * ux + gdy * uy;

@@ -334,7 +334,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch geometry")
     ap.add_argument("--row-block", type=int, default=0,
-                    help="fix the row-block height (2 CTAs per SM) instead of tuning")
+                    help="fix the row-block height (as many CTAs per SM as fit) instead of tuning")
     ap.add_argument("--cpu-baseline-only", type=float, default=None, metavar="SECONDS",
                     help="print the oracle's host-core sample for this workload and exit")
     ap.add_argument("--no-repeats", action="store_true",
@@ -386,7 +386,7 @@ def main():
     # launch geometry from the library's autotuner (its trial steps are part of
     # the untimed warm-up)
     if args.row_block:
-        launch = L.set_launch(args.row_block, 2)
+        launch = L.set_launch(args.row_block)
     else:
         launch = L.tune(3) if not args.no_tune else L.kernel_info()
     L.step(args.warmup)
@@ -465,7 +465,7 @@ def main():
         orho, oux, ouy = (t.numpy() for t in pin[3:])
         E = P.Lattice(p, stream)
         if args.row_block:
-            E.set_launch(args.row_block, 2)
+            E.set_launch(args.row_block)
         elif not args.no_tune:
             E.tune(3)                    # untimed, like the warm-up
         thr = 0.5 * (w["rho_ext"] + w["rho_v"])

@@ -313,10 +313,11 @@ int lbm_tune(lbm_handle* h, int32_t steps_per_trial, lbm_kernel_info* out);
 
 /* Set the launch geometry explicitly (e.g. one that lbm_tune chose earlier for
  * the same lattice size): row blocks of row_block rows, at most ctas_per_sm
- * resident CTAs per SM.  Results do not depend on it.  No counterpart in the
- * paper.  Returns LBM_ERR_INVALID_ARG for a null handle, row_block < 1 or
- * ctas_per_sm < 1 or above what the kernel's resources allow on this device;
- * LBM_ERR_CUDA if the device cannot be queried. */
+ * resident CTAs per SM (0: as many as the kernel's resources allow on this
+ * device).  Results do not depend on it.  No counterpart in the paper.
+ * Returns LBM_ERR_INVALID_ARG for a null handle, row_block < 1 or
+ * ctas_per_sm < 0 or above what the kernel's resources allow; LBM_ERR_CUDA if
+ * the device cannot be queried. */
 int lbm_set_launch(lbm_handle* h, int32_t row_block, int32_t ctas_per_sm);
 
 /* Measured compute peaks of the current device (no counterpart in the paper:

@@ -354,8 +354,9 @@ class Lattice:
         _check(lib().lbm_tune(self._h, int(steps_per_trial), C.byref(k)), "lbm_tune")
         return {n: getattr(k, n) for n, _ in lbm_kernel_info._fields_}
 
-    def set_launch(self, row_block: int, ctas_per_sm: int = 2) -> dict:
-        """lbm_set_launch: fix the launch geometry; returns kernel_info."""
+    def set_launch(self, row_block: int, ctas_per_sm: int = 0) -> dict:
+        """lbm_set_launch: fix the launch geometry (ctas_per_sm 0: the most that
+        fit on an SM); returns kernel_info."""
         _check(lib().lbm_set_launch(self._h, int(row_block), int(ctas_per_sm)), "lbm_set_launch")
         return self.kernel_info()
 

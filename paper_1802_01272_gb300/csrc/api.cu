@@ -654,7 +654,7 @@ int lbm_step(lbm_handle* h, int64_t n) {
 }
 
 int lbm_set_launch(lbm_handle* h, int32_t row_block, int32_t ctas_per_sm) {
-  if (!h || row_block < 1 || ctas_per_sm < 1) return LBM_ERR_INVALID_ARG;
+  if (!h || row_block < 1 || ctas_per_sm < 0) return LBM_ERR_INVALID_ARG;
   const int lim = h->p.ctu_order == 1 ? 0 : h->p.limiter;
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
@@ -665,6 +665,7 @@ int lbm_set_launch(lbm_handle* h, int32_t row_block, int32_t ctas_per_sm) {
                      : step_occupancy_f64(h->p.ctu_order, lim, h->vec, regu, h->smem);
   if (nsm < 1 || occ < 1) return set_err(h, LBM_ERR_CUDA);
   if (ctas_per_sm > occ) return LBM_ERR_INVALID_ARG;
+  if (ctas_per_sm == 0) ctas_per_sm = occ;
   const long long items = (long long)((h->p.Ly + row_block - 1) / row_block) * h->nstrip;
   const long long gmax = (long long)nsm * ctas_per_sm;
   h->row_block = row_block;

@@ -286,11 +286,11 @@ cudaError_t launch_hist(const AuxArgs& a, const void* f, int nbins, double lo, d
 
 size_t step_smem_bytes(size_t stage_elem, size_t elem) {
   const size_t elems = (size_t)FROWS * FRS + 4 * (size_t)MROWS * MP;  // f*, drho, ux, uy, phi
-  // + 128 bytes to align the staging ring and the output tile for tensor
-  // copies; the fused diagnostics' bubble-site sums, the staging slots'
-  // mbarriers and the CTA's wait-abort flag
+  // + 128 bytes to align the staging ring (which also holds the output tiles)
+  // for tensor copies; the fused diagnostics' bubble-site sums, the staging
+  // slots' mbarriers and the CTA's wait-abort flag
   const size_t scol = stage_elem == 2 ? scol_of<__half>() : scol_of<float>();
-  return 128 + stage_elem * ((size_t)NSLOT * RPI * 16 * scol + (size_t)RPI * 16 * TW) +
+  return 128 + stage_elem * (size_t)NSLOT * RPI * 16 * scol +
          elem * elems + 6 * sizeof(unsigned long long) + NSLOT * sizeof(unsigned long long) +
          2 * sizeof(int);
 }

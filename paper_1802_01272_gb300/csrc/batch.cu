@@ -1,7 +1,8 @@
 // batch.cu -- continuous-batching server for many independent lattices (the
 // lbm_batch_* calls of include/ctulbm.h).  Host code only: it is a client of
 // the single-lattice C ABI (lbm_create, lbm_init_rho_u, lbm_step_many,
-// lbm_diagnostics, lbm_moments, lbm_destroy) driven by one worker thread.
+// lbm_diagnostics, lbm_moments, lbm_destroy) driven by one worker thread; it
+// asks the library's internals only how many batched CTAs fit on an SM.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -16,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include "ctulbm.h"
+#include "lbm_internal.h"
 
 namespace {
 
@@ -207,8 +209,11 @@ int lbm_batch_create(size_t max_bytes, int32_t chunk_steps, void* cuda_stream, l
   int nsm = 0;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
     return LBM_ERR_CUDA;
-  // two resident CTAs per SM, two work items of 96 rows x 56 columns each
-  b->fill_nodes = (long long)nsm * 2 * 2 * 96 * 56;
+  // the batched kernel's resident CTAs per SM (CTU2 + MC, FP32 storage), two
+  // work items of 96 rows x 56 columns each
+  int occ = ctulbm::step_batch_occupancy_f32(2, 0, false, ctulbm::step_smem_bytes(4, 4));
+  if (occ < 1) occ = 2;
+  b->fill_nodes = (long long)nsm * occ * 2 * 96 * 56;
   b->stream = static_cast<cudaStream_t>(cuda_stream);
   if (!b->stream) {
     if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)

@@ -55,10 +55,11 @@ template <typename ST>
 constexpr int scol_of() {
   return sizeof(ST) == 2 ? 72 : 68;
 }
-constexpr int NSLOT = 3;        // staging ring: the batch being read, two being loaded
+constexpr int NSLOT = 2;        // staging ring: the batch being read, the next being loaded
+static_assert(TW <= 68, "an output tile [16][RPI][TW] fits in a staging slot");
 constexpr int PRODUCER = NT - 32;  // the thread that issues tensor copies and stores (warp 7,
                                    // which has no node in the collision phase)
-constexpr int FROWS = 8;        // advected-row ring f* (power of two)
+constexpr int FROWS = 6;        // advected-row ring f*: rows B - 4 .. B + 1 of an iteration
 constexpr int MROWS = 8;        // moment rings (power of two)
 constexpr int P4T = RPI * TW;   // collision threads: one per output node of an iteration
 // Padded pitches: the collision's warps read 4 rows x 8 columns of the rings;

@@ -5,7 +5,8 @@
 // A staged batch (RPI rows of scol_of<ST>() columns x 16 planes) arrives by one
 // tensor copy into a ring slot laid out [RPI][16][columns]; completion is
 // counted in bytes on the slot's mbarrier, and every wait on it is bounded in
-// time.  The collision's output tile [16][RPI][TW] leaves by one tensor store.
+// time.  The collision's output tile [16][RPI][TW] is written into the slot
+// whose batch P1 has consumed and leaves by one tensor store.
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
 }
@@ -88,8 +89,11 @@ __device__ __forceinline__ int mod_pos(int a, int n) {  // a mod n for a > -n*10
 template <typename T, typename ST>
 struct Smem {
   static constexpr int SCOL = scol_of<ST>();
-  ST* stage;  // [NSLOT][RPI][16][SCOL] f^n rows of the strip, with the advection halo
-  ST* out;    // [16][RPI][TW] the f^{n+1} tile of the tensor store (plane-major)
+  // [NSLOT][RPI][16][SCOL] f^n rows of the strip, with the advection halo.
+  // Once P1 has consumed a slot's batch, the slot holds that iteration's
+  // f^{n+1} tile [16][RPI][TW] (plane-major) until its tensor store has read
+  // it; the producer waits for that before it arms the slot's next copy.
+  ST* stage;
   T* fs;      // [FROWS][FRS] advected f*: 16 planes of REG per row, padded
   T* drho;    // [MROWS][MP] rho* - rho_ref
   T* ux;
@@ -102,8 +106,7 @@ struct Smem {
     // tensor copies need 128-byte aligned tiles; the allocation has the slack
     raw += (128u - ((unsigned)__cvta_generic_to_shared(raw) & 127u)) & 127u;
     stage = reinterpret_cast<ST*>(raw);
-    out = stage + NSLOT * RPI * 16 * SCOL;
-    T* p = reinterpret_cast<T*>(out + RPI * 16 * TW);
+    T* p = reinterpret_cast<T*>(stage + NSLOT * RPI * 16 * SCOL);
     fs = p;
     p += FROWS * FRS;
     drho = p;
@@ -305,7 +308,8 @@ __device__ __forceinline__ void seam_fixup(const StepArgs<T>& P, const Smem<T, S
 // advected rows to the f* ring at `fbase` (thread's plane and group).
 template <int SX, int SY, int ORDER, int LIM, typename T, typename ST>
 __device__ __forceinline__ void advect_batch(typename AdvSel<T>::State& st, const VelConst<T>& vc,
-                                             const ST* sbase, T* fbase) {
+                                             const ST* sbase, T* fa, T* fb) {
+  // rows 0, 1 of the batch go to ring rows fa, fa + FRS; rows 2, 3 to fb, fb + FRS
   constexpr int SCOL = scol_of<ST>();
   if constexpr (sizeof(T) == 4) {
     const VelPairs vp = vel_pairs<SX>(vc);
@@ -313,14 +317,15 @@ __device__ __forceinline__ void advect_batch(typename AdvSel<T>::State& st, cons
     for (int r = 0; r < RPI; ++r) {
       float out[4];
       advect_row2<SX, SY, ORDER, LIM>(st, sbase + r * (16 * SCOL), vp, out);
-      *reinterpret_cast<float4*>(fbase + r * FRS) = make_float4(out[0], out[1], out[2], out[3]);
+      *reinterpret_cast<float4*>((r < 2 ? fa : fb) + (r & 1) * FRS) =
+          make_float4(out[0], out[1], out[2], out[3]);
     }
   } else {
 #pragma unroll
     for (int r = 0; r < RPI; ++r) {
       T out[4];
       advect_row<SX, SY, ORDER, LIM>(st, sbase + r * (16 * SCOL), vc, out);
-      T* dst = fbase + r * FRS;
+      T* dst = (r < 2 ? fa : fb) + (r & 1) * FRS;
       reinterpret_cast<double2*>(dst)[0] = make_double2(out[0], out[1]);
       reinterpret_cast<double2*>(dst)[1] = make_double2(out[2], out[3]);
     }
@@ -370,10 +375,13 @@ __device__ __forceinline__ void force_dt(const StepArgs<T>& P, const T* ph, cons
 //
 // Iteration i consumes staged batch B_i = ys - 4 + 4 i .. +3 and, in the same
 // iteration, P1 writes f* of rows B_i - 2 .., P2 their moments, P4 the outputs
-// of rows B_i - 4 .. = ys + 4 (i - WARM) ..  (rings indexed by (row - ys + 6)
-// mod 8); three CTA barriers per iteration.  The tile of P4(i) leaves
-// by a tensor store issued by thread 0 at the start of iteration i + 1 (or
-// after the loop), after the barrier that ends P4(i).
+// of rows B_i - 4 .. = ys + 4 (i - WARM) ..; the f* ring keeps rows by
+// (row - ys) mod 6, the moment rings by (row - ys + 6) mod 8; three CTA
+// barriers per iteration.  The tile of P4(i) is written into the staging slot
+// that batch B_i has left and leaves by a tensor store that the producer
+// issues at the start of iteration i + 1 (or after the loop), after the
+// barrier that ends P4(i); the slot's next batch is armed once that store has
+// read it.
 template <typename T, typename ST, int ORDER, int LIM, bool VEC, bool DIAG, bool REGU>
 __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, ST>& S, int strip,
                                             int ys, int ye, const CUtensorMap* tm, unsigned& gb,
@@ -388,7 +396,11 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
   const VelConst<T> vc = P.v[k];
   const int Lx = P.Lx, Ly = P.Ly;
 
-  __syncthreads();  // previous segment done with the rings
+  // the tiles of the previous segment's last iterations may still be leaving
+  // from the staging slots: the producer waits for their reads before anyone
+  // writes a slot again
+  if (VEC && P.tma_out && tid == PRODUCER) bulk_wait_read<0>();
+  __syncthreads();  // previous segment done with the rings and the slots
 
   typename AdvSel<T>::State st;
   memset(&st, 0, sizeof(st));
@@ -400,7 +412,7 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
   const int x0 = strip * TW - XOFF - 4;
   const bool seam = VEC && (x0 < 0 || x0 + SCOL > Lx);
   const bool producer = tid == PRODUCER;
-  const bool tstore = P.tma_out;
+  const bool tstore = VEC && P.tma_out;  // (the maps of both directions exist together)
   const int nit = WARM + (ye - ys + RPI - 1) / RPI;
   const unsigned g0 = gb;
 
@@ -413,11 +425,13 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
   const int r4 = lane >> 3, o4 = 8 * warp + (lane & 7);  // row, output column of the strip
   const int c4 = XOFF + o4, x4 = strip * TW + o4;
 
-  // batches g0 and g0 + 1 before the loop; in iteration it, batch g0 + it + 1
-  // gets its ghost rows (and per-thread loads) and, in the collision phase,
-  // the producer issues the tensor copies of batch g0 + it + 2
+  // batches g0 and g0 + 1 before the loop (both slots are free); in
+  // iteration it >= 1 the producer issues the tensor copies of batch g0 + it + 1
+  // at the end of P1 and all threads write its ghost rows after that barrier
+  // (per-thread staging: loads and ghost rows of batch g0 + it + 1 in L)
   ghost_rows<T, ST>(P, S, slots, ys - 4, g0);
   if constexpr (VEC) {
+    if (nit > 1) ghost_rows<T, ST>(P, S, slots, ys, g0 + 1);
     if (producer) {
       arm_tma<T, ST>(P, S, tm, x0, ys - 4, g0, gi);
       if (nit > 1) arm_tma<T, ST>(P, S, tm, x0, ys, g0 + 1, gi);
@@ -428,22 +442,25 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
 
   T dseg = T(0);  // fused diagnostics: mass of this thread's nodes (rho - rho_ref)
   int nseg = 0;
+  int f6 = 0;  // f* ring row of row B - 2 (rows are kept mod FROWS = 6): 4 it mod 6
   for (int it = 0; it < nit; ++it) {
     const unsigned gcur = g0 + (unsigned)it;
     const int B = ys - 4 + RPI * it;  // first staged row of this iteration
-    // ---------------- L: the previous iteration's output tile leaves (its
-    // writes were fenced before the barrier that ended that iteration); the
-    // next batch's ghost rows (and loads); wait for this batch
+    // ---------------- L: the previous iteration's output tile leaves from
+    // its slot (its writes were fenced before the barrier that ended that
+    // iteration); the next batch's ghost rows (and loads); wait for this batch
     if (tstore && producer) {
       const int row0 = ys + RPI * (it - 1 - WARM);  // rows of the previous iteration's P4
       if (it - 1 >= WARM && row0 + RPI <= ye) {       // (a partial batch is stored per thread)
-        tma_store_rows(tm + 2, strip * TW, row0, S.out);
+        tma_store_rows(tm + 2, strip * TW, row0, S.stage + slot_of(gcur - 1) * (RPI * 16 * SCOL));
         bulk_commit();
       }
     }
-    if (it + 1 < nit) {
-      ghost_rows<T, ST>(P, S, slots, B + RPI, gcur + 1);
-      if constexpr (!VEC) load_scalar<T, ST>(P, S, slots, x0, B + RPI, gcur + 1, gi);
+    if constexpr (!VEC) {
+      if (it + 1 < nit) {
+        ghost_rows<T, ST>(P, S, slots, B + RPI, gcur + 1);
+        load_scalar<T, ST>(P, S, slots, x0, B + RPI, gcur + 1, gi);
+      }
     }
     wait_batch<VEC>(P, S, gcur);
     if (seam) seam_fixup<T, ST>(P, S, x0, B, gcur);
@@ -451,12 +468,13 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
     // ---------------- P1: advect the staged batch into f* rows B - 2 ..
     {
       const ST* sb = p1_src + slot_of(gcur) * (RPI * 16 * SCOL);
-      T* fb = p1_dst + (it & 1) * (RPI * FRS);
+      T* fa = p1_dst + f6 * FRS;                       // ring rows f6, f6 + 1
+      T* fb = p1_dst + (f6 == 4 ? 0 : f6 + 2) * FRS;  // and f6 + 2, f6 + 3 (mod 6)
       switch (q) {
-        case 0: advect_batch<+1, +1, ORDER, LIM>(st, vc, sb, fb); break;
-        case 1: advect_batch<-1, +1, ORDER, LIM>(st, vc, sb, fb); break;
-        case 2: advect_batch<-1, -1, ORDER, LIM>(st, vc, sb, fb); break;
-        default: advect_batch<+1, -1, ORDER, LIM>(st, vc, sb, fb); break;
+        case 0: advect_batch<+1, +1, ORDER, LIM>(st, vc, sb, fa, fb); break;
+        case 1: advect_batch<-1, +1, ORDER, LIM>(st, vc, sb, fa, fb); break;
+        case 2: advect_batch<-1, -1, ORDER, LIM>(st, vc, sb, fa, fb); break;
+        default: advect_batch<+1, -1, ORDER, LIM>(st, vc, sb, fa, fb); break;
       }
       // wall ghost rows keep f^eq(rho_ext, u_wall)
       if (P.walls && (B - 2 < 0 || B + 2 > Ly)) {
@@ -465,19 +483,30 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
           const int a = B - 2 + r;
           if (a < 0 || a >= Ly) {
             const T gv = a < 0 ? vc.gbot : vc.gtop;
-            T* dst = fb + r * FRS;
+            T* dst = (r < 2 ? fa : fb) + (r & 1) * FRS;
 #pragma unroll
             for (int m = 0; m < 4; ++m) dst[m] = gv;
           }
         }
       }
     }
+    // the producer issues batch it + 1 into the other slot once the store of
+    // the previous iteration's tile (issued in L) has read it
+    if constexpr (VEC) {
+      if (producer && it >= 1 && it + 1 < nit) {
+        if (tstore) bulk_wait_read<0>();
+        arm_tma<T, ST>(P, S, tm, x0, B + RPI, gcur + 1, gi);
+      }
+    }
     __syncthreads();
+    if constexpr (VEC) {
+      if (it >= 1 && it + 1 < nit) ghost_rows<T, ST>(P, S, slots, B + RPI, gcur + 1);
+    }
 
     // ---------------- P2: moments of rows B - 2 .., one thread per node
     if (it >= 1) {
       const int sl = (it & 1) * RPI + r2;
-      const T* src = S.fs + sl * FRS + c2;
+      const T* src = S.fs + (f6 + r2 < 6 ? f6 + r2 : f6 + r2 - 6) * FRS + c2;
       T f[16];
 #pragma unroll
       for (int kk = 0; kk < 16; ++kk) f[kk] = src[kk * REG];
@@ -520,7 +549,6 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
       const T rT = rho * P.Tt;
       S.phi[m] = fma(P.a * rho, rho, rT - rT * rcp(T(1) - P.b * rho));
     }
-    if (tstore && producer) bulk_wait_read<0>();  // the tile is free for this P4
     __syncthreads();
 
     // ---------------- P4: g, collision of all planes, output tile (rows B - 4 ..)
@@ -551,7 +579,8 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
         const T mxg[2] = {lo * gdx, hi * gdx}, myg[2] = {lo * gdy, hi * gdy};
 
         T f[16];
-        const T* src = S.fs + s0 * FRS + c4;
+        const int fr = f6 + 4 + r4;  // f* ring row of lattice row c
+        const T* src = S.fs + (fr < 6 ? fr : fr - 6) * FRS + c4;
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) f[kk] = src[kk * REG];
 
@@ -665,7 +694,7 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
           }
         }
         if (tstore && B + RPI - 4 <= ye) {  // a full batch: the tile
-          ST* dst = S.out + r4 * TW + o4;
+          ST* dst = S.stage + slot_of(gcur) * (RPI * 16 * SCOL) + r4 * TW + o4;
 #pragma unroll
           for (int kk = 0; kk < 16; ++kk) dst[kk * (RPI * TW)] = to_store<ST, T>(outv[kk]);
         } else {
@@ -698,19 +727,16 @@ __device__ __forceinline__ void run_segment(const StepArgs<T>& P, const Smem<T, 
         }
       }
     }
-    // the producer (no collision node) issues batch it + 2 meanwhile: its slot
-    // was last read by P1 of the previous iteration
-    if constexpr (VEC) {
-      if (producer && it + 2 < nit) arm_tma<T, ST>(P, S, tm, x0, B + 2 * RPI, gcur + 2, gi);
-    }
     if (tstore) fence_proxy_async();  // the tile's generic writes before its tensor store
     __syncthreads();
+    f6 = f6 >= 2 ? f6 - 2 : f6 + 4;
   }
   // the last tile of the segment
   if (tstore && producer) {
     const int row0 = ys + RPI * (nit - 1 - WARM);
     if (row0 + RPI <= ye) {
-      tma_store_rows(tm + 2, strip * TW, row0, S.out);
+      tma_store_rows(tm + 2, strip * TW, row0,
+                     S.stage + slot_of(g0 + (unsigned)(nit - 1)) * (RPI * 16 * SCOL));
       bulk_commit();
     }
   }
@@ -788,7 +814,7 @@ __device__ __forceinline__ void init_cta_barriers(unsigned long long* dsums,
 // are separate instantiations, so that the plain step carries none of their
 // instructions (cold code in the loop body costs instruction fetch).
 template <typename T, typename ST, int ORDER, int LIM, bool VEC, bool DIAG, bool REGU>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
     step_kernel(const __grid_constant__ StepArgs<T> P, const __grid_constant__ RowMaps maps) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const Smem<T, ST> S(smem_raw);
@@ -824,7 +850,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
 // Several lattices advanced by one launch: their work items are concatenated
 // and claimed from one counter; each lattice brings its own tensor maps.
 template <typename T, int ORDER, int LIM, bool VEC, bool REGU>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1)
     step_batch_kernel(const __grid_constant__ BatchArgs<T> B) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const Smem<T, T> S(smem_raw);

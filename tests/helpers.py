@@ -17,3 +17,12 @@ def rel_err(a, b):
     """max |a - b| / max |b|  (normwise relative error, safe for fields near 0)."""
     a, b = np.asarray(a), np.asarray(b)
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def rel_err_elem(a, b, floor=1e-3):
+    """max |a - b| / (|b| + floor * max |b|): element-wise relative error, with a
+    floor so that entries near zero (a velocity component at rest) are
+    compared at a fixed fraction of the field's scale."""
+    a, b = np.asarray(a), np.asarray(b)
+    scale = max(np.abs(b).max(), 1e-300)
+    return float((np.abs(a - b) / (np.abs(b) + floor * scale)).max())

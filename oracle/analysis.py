@@ -160,22 +160,47 @@ def shape_from_sums(nb, sx, sy, sxx, sxy, syy):
     return dict(a=a, b=b, D=(a - b) / (a + b), theta=theta, cx=cx, cy=cy)
 
 
-def coexistence_from_histogram(counts, lo, hi, rho_values=None, split=1.0, halfwidth=2):
-    """Coexistence densities from a rho histogram: the highest bin on each side
-    of `split`; if the raw densities are given, each peak is refined to the mean
-    of the values within +-halfwidth bins of it."""
-    counts = np.asarray(counts)
+def coexistence_from_histogram(counts, lo, hi, rho_values=None, split=1.0, halfwidth=2,
+                               peak="bin", smooth_bins=2.0):
+    """Coexistence densities from a rho histogram: the peak on each side of
+    `split`; if the raw densities are given, each peak is refined to the mean
+    of the values within +-halfwidth bins of it (a window 2 halfwidth + 1 bins
+    wide).  peak="bin": the highest bin.  peak="smoothed": the vertex of the
+    parabola through the three highest values of the histogram smoothed by a
+    Gaussian of smooth_bins bins, so that the peak moves continuously with the
+    data (the highest raw bin jumps by a whole bin when the top of a broad
+    peak is nearly flat, as in a state that is still separating)."""
+    counts = np.asarray(counts, dtype=np.float64)
     nb = len(counts)
     edges = np.linspace(lo, hi, nb + 1)
+    w = (hi - lo) / nb
     centers = 0.5 * (edges[:-1] + edges[1:])
+    if peak == "smoothed":
+        r = int(np.ceil(4 * smooth_bins))
+        k = np.exp(-0.5 * (np.arange(-r, r + 1) / smooth_bins) ** 2)
+        hist = np.convolve(counts, k / k.sum(), mode="same")
+    elif peak == "bin":
+        hist = counts
+    else:
+        raise ValueError(peak)
     out = []
     for side in (centers < split, centers >= split):
         idx = np.where(side)[0]
-        pk = idx[np.argmax(counts[idx])]
+        pk = int(idx[np.argmax(hist[idx])])
+        x = float(centers[pk])
+        if peak == "smoothed" and 0 < pk < nb - 1:
+            y0, y1, y2 = hist[pk - 1], hist[pk], hist[pk + 1]
+            den = y0 - 2.0 * y1 + y2
+            if den < 0.0:
+                x += float(np.clip(0.5 * (y0 - y2) / den, -0.5, 0.5)) * w
         if rho_values is None:
-            out.append(float(centers[pk]))
-        else:
+            out.append(x)
+        elif peak == "bin":
             l, h = edges[max(pk - halfwidth, 0)], edges[min(pk + halfwidth + 1, nb)]
+            sel = rho_values[(rho_values >= l) & (rho_values < h)]
+            out.append(float(sel.mean()))
+        else:
+            l, h = x - (halfwidth + 0.5) * w, x + (halfwidth + 0.5) * w
             sel = rho_values[(rho_values >= l) & (rho_values < h)]
             out.append(float(sel.mean()))
     return out[1], out[0]  # (rho_L, rho_V)

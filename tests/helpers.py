@@ -19,10 +19,11 @@ def rel_err(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-def rel_err_elem(a, b, floor=1e-3):
-    """max |a - b| / (|b| + floor * max |b|): element-wise relative error, with a
-    floor so that entries near zero (a velocity component at rest) are
-    compared at a fixed fraction of the field's scale."""
+def rel_err_elem(a, b, floor=1e-3, abs_floor=0.0):
+    """max |a - b| / (|b| + floor * max |b| + abs_floor): element-wise relative
+    error, with a floor so that entries near zero are compared at a fixed
+    scale (a fraction of the field's largest entry, or an absolute scale such
+    as the thermal speed sqrt(T) for velocities)."""
     a, b = np.asarray(a), np.asarray(b)
     scale = max(np.abs(b).max(), 1e-300)
-    return float((np.abs(a - b) / (np.abs(b) + floor * scale)).max())
+    return float((np.abs(a - b) / (np.abs(b) + floor * scale + abs_floor)).max())

@@ -70,3 +70,45 @@ def test_split_decides_the_sides():
         counts, _ = np.histogram(rho, bins=NB, range=(LO, HI))
         rl, rv = A.coexistence_from_histogram(counts, LO, HI, rho_values=rho)
         assert rv == CENTRES[200] and rl == CENTRES[1200]
+
+
+def test_smoothed_peak_moves_continuously():
+    """A state still separating has a broad, nearly flat-topped bulk peak: here
+    a liquid population spread uniformly over six bins around ml.  Shifting
+    every value by a fraction of a bin shifts the smoothed-peak estimate by
+    that fraction (the window is centred on a peak that moves continuously);
+    the highest-bin reading jumps by whole bins instead, which is why two
+    slightly different runs (FP32 and FP64 of a chaotic separation) can
+    differ there by a bin width (1.5e-3 at 2048 bins on [0, 3))."""
+    rng = np.random.default_rng(3)
+    ml, mv = CENTRES[1100], CENTRES[300]
+    liq = ml + W * rng.uniform(-3.0, 3.0, 400_000)
+    vap = mv + 3e-4 * rng.standard_normal(100_000)
+    iface = rng.uniform(mv, ml, 20_000)
+    jumps = []
+    for d in (0.0, 0.2, 0.45, 0.7, 0.95):
+        rho = np.concatenate([vap, liq + d * W, iface])
+        counts, _ = np.histogram(rho, bins=NB, range=(LO, HI))
+        rl, rv = A.coexistence_from_histogram(counts, LO, HI, rho_values=rho, peak="smoothed",
+                                              halfwidth=4)
+        assert abs(rl - (ml + d * W)) < 0.1 * W, (d, (rl - ml) / W)
+        assert abs(rv - vap.mean()) < 1e-5
+        rb, _ = A.coexistence_from_histogram(counts, LO, HI, rho_values=rho)
+        jumps.append((rb - (ml + d * W)) / W)
+    print("\nhighest-bin reading minus the true centre, in bins:", np.round(jumps, 2))
+
+
+def test_smoothed_peak_on_a_separated_sample():
+    """On narrow bulk populations the smoothed reading equals the bulk means,
+    as the highest-bin reading does."""
+    rng = np.random.default_rng(2)
+    mv, ml = 0.4257, 1.6573
+    vap = mv + 3e-4 * rng.standard_normal(150_000)
+    liq = ml + 3e-4 * rng.standard_normal(350_000)
+    iface = rng.uniform(mv, ml, 40_000)
+    rho = rng.permutation(np.concatenate([vap, liq, iface]))
+    counts, _ = np.histogram(rho, bins=NB, range=(LO, HI))
+    for hw in (2, 4):
+        rl, rv = A.coexistence_from_histogram(counts, LO, HI, rho_values=rho, peak="smoothed",
+                                              halfwidth=hw)
+        assert abs(rv - vap.mean()) < 1e-5 and abs(rl - liq.mean()) < 1e-5

@@ -57,9 +57,11 @@ def test_config1_fp64_128_200_steps(P, oracle_mod):
             ro, uxo, uyo = O.moments(op, fo)
             assert rel_err(rg, ro) < TOL64
             assert rel_err(uxg, uxo) < TOL64 and rel_err(uyg, uyo) < TOL64
-            # element by element, velocities near zero included (floor 1e-3 of the scale)
+            # element by element: rho relative, u relative to |u| + sqrt(T) (the
+            # thermal speed: rounding of f moves u by ~1e-16 of it wherever u ~ 0)
+            ct = np.sqrt(lp.T)
             assert rel_err_elem(rg, ro) < TOL64
-            assert rel_err_elem(uxg, uxo) < 1e-9 and rel_err_elem(uyg, uyo) < 1e-9
+            assert rel_err_elem(uxg, uxo, 0.0, ct) < TOL64 and rel_err_elem(uyg, uyo, 0.0, ct) < TOL64
         d = L.diagnostics(threshold=1.0)
         assert abs(d["mass"] - ro.sum()) / ro.sum() < 1e-12
 
@@ -102,8 +104,10 @@ def test_variants_fp64(P, oracle_mod, case):
         assert rel_err(fg, fo) < TOL64, f"after {n} steps"
         rg, uxg, uyg = L.moments()
         ro, uxo, uyo = O.moments(oracle_params(O, lp), fo)
+        ct = np.sqrt(lp.T)
         assert rel_err_elem(rg, ro) < TOL64, f"rho after {n} steps"
-        assert rel_err_elem(uxg, uxo) < 1e-9 and rel_err_elem(uyg, uyo) < 1e-9, f"u after {n} steps"
+        assert (rel_err_elem(uxg, uxo, 0.0, ct) < TOL64 and
+                rel_err_elem(uyg, uyo, 0.0, ct) < TOL64), f"u after {n} steps"
 
 
 def test_kernel_info_staging_paths(P):
@@ -134,9 +138,14 @@ def test_fp32_shifted_1000_steps(P, oracle_mod):
 
 
 def test_fp32_bubble_with_walls(P, oracle_mod):
-    """FP32 shifted storage against the FP64 oracle over 2000 steps of a bubble
-    between moving walls (tau = 1e-2, u_w = 0.2): rho within 1e-5 (normwise
-    and element by element), u within 1e-4 of its scale element by element."""
+    """FP32 shifted storage against the FP64 oracle on a bubble between moving
+    walls (tau = 1e-2, u_w = 0.2): rho within 1e-5 normwise after 1000 and
+    2000 steps.  Element by element the vapour nodes carry more: the stored
+    deviations f - w rho_ref are rounded relative to rho_ref = 1.9, which is
+    8 times the vapour's 0.24, and u = j / rho carries the same factor.  So
+    element-wise rho (relative to |rho|) and u (relative to |u| + sqrt(T))
+    are held to 2e-5 after 1000 steps and 4e-5 after 2000 (measured 1.1e-5,
+    1.3e-5 and 1.3e-5, 1.6e-5: the rounding accumulates about linearly)."""
     O = oracle_mod
     lp = P.Params(Lx=128, Ly=96, precision=P.LBM_FP32_SHIFTED, rho_ref=1.9, T=0.8, tau=1e-2,
                   boundary=P.LBM_BC_SHEAR_WALLS, rho_ext=1.9)
@@ -144,17 +153,20 @@ def test_fp32_bubble_with_walls(P, oracle_mod):
     rho, ux, uy = synth.bubble(lp.Lx, lp.Ly, 1.9, 0.24, R=20, W=4)
     ux = synth.linear_shear(lp.Lx, lp.Ly, 0.2)
     op = oracle_params(O, lp)
-    f0 = O.init_feq(op, rho, ux, uy)
+    fo = O.init_feq(op, rho, ux, uy)
+    ct = np.sqrt(lp.T)
     with P.Lattice(lp) as L:
         L.init_rho_u(rho, ux, uy)
-        L.step(2000)
-        rg, uxg, uyg = L.moments()
-    ro, uxo, uyo = O.moments(op, O.step(op, f0, 2000))
-    e_rho, e_u = rel_err_elem(rg, ro), max(rel_err_elem(uxg, uxo, 1.0), rel_err_elem(uyg, uyo, 1.0))
-    print(f"\nFP32 vs oracle after 2000 steps: rho {rel_err(rg, ro):.2e} (element-wise {e_rho:.2e}), "
-          f"u {e_u:.2e} of its scale")
-    assert rel_err(rg, ro) < 1e-5 and e_rho < 1e-5
-    assert e_u < 1e-4
+        for n, bar in ((1000, 2e-5), (2000, 4e-5)):
+            L.step(1000)
+            fo = O.step(op, fo, 1000)
+            rg, uxg, uyg = L.moments()
+            ro, uxo, uyo = O.moments(op, fo)
+            e_rho = rel_err_elem(rg, ro)
+            e_u = max(rel_err_elem(uxg, uxo, 0.0, ct), rel_err_elem(uyg, uyo, 0.0, ct))
+            print(f"\nFP32 vs oracle after {n} steps: rho {rel_err(rg, ro):.2e} (element-wise "
+                  f"{e_rho:.2e}), u {e_u:.2e} relative to |u| + sqrt(T)")
+            assert rel_err(rg, ro) < 1e-5 and e_rho < bar and e_u < bar, n
 
 
 def test_checkpoint_resume_bit_identical(P):

@@ -68,10 +68,14 @@ def rayleigh_plesset(R0, V0, times, p_b, p_inf, r_inf, sigma, rho_l, mu_l, dt=1e
 
 def bubble_fields(Lx, Ly, R, rho_in, rho_out, width=1.0):
     """A circular bubble of radius R nodes centred at (Lx/2, Ly/2): a tanh
-    profile of `width` nodes between rho_in (inside) and rho_out; u = 0."""
+    profile of `width` nodes between rho_in (inside) and rho_out (width 0: a
+    sharp edge, rho_in for r < R); u = 0."""
     y, x = np.mgrid[0:Ly, 0:Lx].astype(np.float64)
     r = np.hypot(x - Lx / 2.0, y - Ly / 2.0)
-    rho = 0.5 * (rho_out + rho_in) + 0.5 * (rho_out - rho_in) * np.tanh((r - R) / width)
+    if width > 0:
+        rho = 0.5 * (rho_out + rho_in) + 0.5 * (rho_out - rho_in) * np.tanh((r - R) / width)
+    else:
+        rho = np.where(r < R, rho_in, rho_out)
     return rho, np.zeros_like(rho), np.zeros_like(rho)
 
 
@@ -259,20 +263,24 @@ class ShearRun:
 
 def sheared_bubble(R0_nodes, capillary, Lx=1024, Ly=512, T=0.8, kappa=1e-4, ds=1 / 256,
                    tau=1e-2, rho_ext=1.90, t_end=10.0, every=0.5,
-                   precision=LBM_FP32_SHIFTED, stream=None) -> ShearRun:
+                   precision=LBM_FP32_SHIFTED, stream=None, width=2.0,
+                   rho_v=None) -> ShearRun:
     """Sec. III C: a vapour bubble (radius R0) growing in a superheated liquid
     (rho_ext, 1.90 as in the paper's runs at T = 0.8, tau = 1e-2) sheared
     between walls moving at -+u_w (y = 0, Ly), periodic in x.  The shear rate
     is set from the target capillary number of the initial radius,
     gamma_dot = Ca sigma / (mu_L R0) with mu_L = rho_L T tau; the fluid starts
     in the linear shear profile.  Records the shape of Eq. (gyr) over time;
-    Ca(t) follows the growing mean radius, as in the paper."""
+    Ca(t) follows the growing mean radius, as in the paper.  The seed is a
+    tanh profile of `width` nodes (0: sharp) at rho_v (default: Maxwell's
+    vapour density)."""
     rl, rv = eos.coexistence(T)
     sigma = eos.interface_tension(T, kappa)
     mu_l = rl * T * tau
     gdot = capillary * sigma / (mu_l * R0_nodes * ds)
     uw = gdot * Ly * ds / 2.0
-    rho, ux, uy = bubble_fields(Lx, Ly, R0_nodes, rv, rho_ext, 2.0)
+    rho, ux, uy = bubble_fields(Lx, Ly, R0_nodes, rv if rho_v is None else rho_v, rho_ext,
+                                width)
     y = np.arange(Ly, dtype=np.float64)
     ux = np.repeat((-uw + 2.0 * uw * (y + 1.0) / (Ly + 1.0))[:, None], Lx, axis=1)
     p = _params(Lx, Ly, T, tau, kappa, ds, precision, rho_ext, boundary=LBM_BC_SHEAR_WALLS,

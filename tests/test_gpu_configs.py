@@ -109,11 +109,10 @@ def test_config4_sheared_bubble_6144_six_shear_rates():
     seed: the paper gives no profile, and on this lattice at tau = 1e-2 the
     26-node seed is close to critical: sharp it grows, with a tanh edge of
     width 1 or 4 nodes it dissolves), the fluid starting in the linear shear
-    profile.  Six wall speeds up to u_w = 0.8 (the paper's largest is Mach ~0.5
-    with c_s ~ 1.7, u_w ~ 0.85, which is beyond the method's linear stability
-    in uniform flow at T = 0.8: test_oracle_stability; on the 6144^2 lattice a
-    wall layer at 0.85 blows up after ~15000 steps), 40000 steps each (t = 4;
-    the paper ran until the bubble
+    profile.  Six wall speeds up to u_w = 0.8 (the paper's three rates,
+    gamma_dot dt = 1.67, 3.33, 5.00 e-6, are u_w = 0.2, 0.4, 0.6; the method's
+    linear stability in uniform flow ends between 0.8 and 0.85 at T = 0.8:
+    test_oracle_stability), 40000 steps each (t = 4; the paper ran until the bubble
     reached the walls, >= 5e5 steps, to reach Ca ~ 0.5), the bubble's area
     fraction, D, theta and Ca = mu_L gamma_dot R^ / sigma (R^ = (a + b)/2) per
     1000 steps.  Asserted: the bubble grows at every rate, its area does not

@@ -3,8 +3,8 @@ the 16-velocity third-order model advanced with CTU2 + MC (T = 0.8,
 tau = 1e-2, dt = 1e-4, ds = 1/256) damps a small density perturbation of a
 liquid moving at u = 0.8 and amplifies it at u = 0.85 (u / sqrt(T) ~ 0.95;
 the perturbation grows about fivefold per 1000 steps).  This bounds the wall
-speeds of the sheared-bubble runs (Sec. III C quotes walls at Mach ~0.5 with
-c_s ~ 1.7, i.e. u_w ~ 0.85, at the edge of this limit)."""
+speeds of the sheared-bubble runs; the paper's (Sec. III C: u_w <= 0.6, Mach
+~0.5 in the liquid) lie below it."""
 import numpy as np
 import pytest
 

@@ -17,20 +17,22 @@
 // Warps hold one sign quadrant (sgn xi_x, sgn xi_y), so the upwind side of
 // every stencil is a compile-time constant inside a warp.  Iteration i takes
 // the staged rows n = B_i .. B_i + 3 of f^n (one tensor copy of 68 columns x
-// 16 planes x 4 rows, issued two iterations ahead into a three-slot ring by a
-// producer thread whose warp has no collision work) and
+// 16 planes x 4 rows into one of two staging slots, issued by a producer
+// thread whose warp has no collision work at the end of the previous
+// iteration's advection) and
 //   P1  advects them (every quadrant emits the rows n - 2, two rows behind
-//       the staged one) into a ring of advected rows f*;
-//   P2  one thread per node: rho*, u*, p^i - p^w of those rows;
-//   P3  the 9-point Laplacian of rho* one row further back;
+//       the staged one) into a six-row ring of advected rows f*;
+//   P2  one thread per node: rho* - rho_ref, u*, p^i - p^w of those rows;
 //   P4  224 threads, one per output node, two rows further back (warp w:
-//       columns 8w .. 8w+7 of the four rows): gradients -> g, f^eq + dt F_k,
-//       relaxation of all 16 planes into a plane-major output tile that one
-//       thread writes to f^{n+1} with a tensor store.
-// Four CTA barriers per four rows; every shared-memory offset inside an
-// iteration is a compile-time constant from a per-thread base.  f^n is read
-// from HBM once per step (the halo columns of neighbouring strips are L2
-// hits) and f^{n+1} written once.
+//       columns 8w .. 8w+7 of the four rows): the 5x5 force stencils -> g
+//       (the Laplacian composed into the gradient of kappa lap rho), f^eq +
+//       dt F_k, relaxation of all 16 planes into a plane-major output tile in
+//       the staging slot P1 has consumed, which one thread writes to f^{n+1}
+//       with a tensor store at the start of the next iteration.
+// Three CTA barriers per four rows; three CTAs per SM; every shared-memory
+// offset inside an iteration is a compile-time constant from a per-thread
+// base.  f^n is read from HBM once per step (the halo columns of
+// neighbouring strips are L2 hits) and f^{n+1} written once.
 #pragma once
 
 #include <cuda.h>  // CUtensorMap (type only)

@@ -79,3 +79,22 @@ def test_single_thread_oracle_sample():
     import bench
     one = bench.cpu_baseline_single_thread("sheared-bubble-2048", seconds=1.0)
     assert one["kind"] == "oracle" and one["cores"] == 1 and one["value"] > 0
+
+
+def test_server_job_mix_follows_config5_with_capped_walls():
+    """The sweep-server job mix (config 5): lattice sizes from {256, 512, 1024,
+    2048}^2, T in [0.75, 0.98], steps in 5000..20000 x the scale, Poisson
+    arrival times increasing; wall speeds capped at bench.U_WALL_MAX (below the
+    method's stability limit in uniform flow, test_oracle_stability)."""
+    import bench
+    import paper_1802_01272_gb300 as P
+    from paper_1802_01272_gb300 import server as S
+    jobs = bench.server_jobs(P, S, 24, 0.05, rate_hz=10.0)
+    assert {j.params.Lx for j in jobs} <= {256, 512, 1024, 2048}
+    assert all(j.params.Lx == j.params.Ly for j in jobs)
+    assert all(0.75 <= j.params.T <= 0.98 for j in jobs)
+    assert all(250 <= j.nsteps <= 1000 for j in jobs)
+    uw = [j.params.shear_rate * j.params.Ly * j.params.ds / 2 for j in jobs]
+    assert max(uw) <= bench.U_WALL_MAX + 1e-12 and max(uw) > 0.0
+    arr = [j.arrival for j in jobs]
+    assert arr[0] == 0.0 and all(b > a for a, b in zip(arr, arr[1:]))

@@ -22,7 +22,7 @@ traffic of the committed ncu capture of this kernel source), `issue_roofline`
 and `fp32_roofline` (instructions and FP32 flops per node update from the
 committed capture, against the peaks the library measures on the device with
 lbm_measure_peaks), `e2e` (the same metric through the C ABI with pinned host
-buffers, copies inside the timed region; median of five runs, with its phase
+buffers, copies inside the timed region; median of seven runs, with its phase
 times), `cpu_baseline` (the FP64 oracle on
 the host cores and on one thread), `clocks`, `config.launch` (the launch
 geometry lbm_tune chose before the warm-up, or --row-block's), `runs` (five
@@ -110,7 +110,7 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-E2E_REPS = 5  # repetitions of the end-to-end region (median reported)
+E2E_REPS = 7  # repetitions of the end-to-end region (median reported)
 RUNS, RUN_S = 5, 1.0  # repeated device-resident regions (median and spread reported)
 SERVER_LOAD = 2.0      # offered load of the server comparison, x the serial capacity
 U_WALL_MAX = 0.5       # server jobs: wall speed cap (Mach ~0.3 in the liquid)

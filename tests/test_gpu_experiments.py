@@ -171,10 +171,12 @@ def test_rayleigh_plesset_growth():
 def test_sheared_bubble_deformation_and_tilt():
     """Sec. III C: a bubble growing in sheared superheated liquid (1024 x 512,
     walls, rho_ext = 1.90, tau = 1e-2) deforms linearly with the capillary
-    number of its current size for Ca <= 0.2 (the paper fits D = 0.89 Ca;
-    Taylor's steady value is 1.02 Ca), tilts at ~pi/4 to the flow at first and
-    less as it grows, less at the higher shear rate, and grows at a rate that
-    does not depend on the shear."""
+    number of its current size for Ca <= 0.2 (the paper fits D = 0.89 Ca,
+    Taylor's steady value is 1.02 Ca; measured here 0.854, bar 0.06; on the
+    paper's 6144^2 lattice at its shear rates the joint slope is 0.95, see
+    test_gpu_configs), tilts at ~pi/4 to the flow at first and less as it
+    grows, less at the higher shear rate, and grows at a rate that does not
+    depend on the shear."""
     from paper_1802_01272_gb300 import experiments as X
     gold = GOLD["shear_deformation_T0.8"]
     lo = X.sheared_bubble(40, 0.05, t_end=10.0, every=1.0)
@@ -185,7 +187,7 @@ def test_sheared_bubble_deformation_and_tilt():
     sel = (lo.t >= 3.0) & (lo.Ca <= 0.2)
     slope = float(np.sum(lo.D[sel] * lo.Ca[sel]) / np.sum(lo.Ca[sel] ** 2))
     print(f"  D = {slope:.3f} Ca (paper {gold['D_over_Ca_fit']}, Taylor {gold['D_over_Ca_taylor']})")
-    assert abs(slope - gold["D_over_Ca_fit"]) < 0.15
+    assert abs(slope - gold["D_over_Ca_fit"]) < 0.06   # measured 0.854
     assert abs(lo.theta[1] - np.pi / 4) < 0.1 and abs(hi.theta[1] - np.pi / 4) < 0.15
     assert lo.theta[-1] < lo.theta[2] and hi.theta[-1] < lo.theta[-1]
     assert lo.R[-1] > 2.5 * lo.R[0]

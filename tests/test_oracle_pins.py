@@ -383,7 +383,9 @@ def test_oracle_planar_vapour_density_at_T06_against_paper(oracle_mod):
     """Sec. II E: on the paper's grid (CTU2, tau = 1e-3, dt = 1e-4,
     ds = 1/256) the planar interface's vapour density at T = 0.6 sits about
     8 % under the Maxwell value.  The oracle's relaxed slab (48 nodes, one
-    row, t = 3, converged to 4e-4): -9.9 %, liquid within 2e-3.  The 3x3
+    row, t = 3, converged to 4e-4), bulk plateaus: vapour -9.3 %, liquid
+    -2.6e-3 (the extremes, -9.9 % and -1.5e-3, include the overshoot beside
+    the interfaces); the bar is 2.5 points around the paper's "about 8 %".  The 3x3
     pressure gradient gives -30 % here."""
     from oracle import analysis as A
     O = oracle_mod
@@ -397,9 +399,14 @@ def test_oracle_planar_vapour_density_at_T06_against_paper(oracle_mod):
     p = params(O, Lx=Lx, Ly=1, T=T, tau=1e-3, dt=1e-4, ds=1 / 256)
     f = O.init_feq(p, prof[None, :], np.zeros((1, Lx)), np.zeros((1, Lx)))
     r, _, _ = O.moments(p, O.step(p, f, 30000))
-    dev_v, dev_l = 1.0 - r.min() / rv, r.max() / rl - 1.0
-    print(f"\nT={T}: rho_V {-dev_v:+.3e} rho_L {dev_l:+.3e} of Maxwell (paper: about -{g['vapour_rel_diff_at_T_low']})")
-    assert abs(dev_v - g["vapour_rel_diff_at_T_low"]) < 0.04 and abs(dev_l) < 2e-3
+    r = r[0]
+    # plateau medians, 3 nodes either side of the bulk centres (x = Lx/2 liquid, x = 0 vapour)
+    liq = np.median(r[Lx // 2 - 3:Lx // 2 + 4])
+    vap = np.median(np.concatenate([r[-3:], r[:4]]))
+    dev_v, dev_l = 1.0 - vap / rv, liq / rl - 1.0
+    print(f"\nT={T}: rho_V {-dev_v:+.3e} rho_L {dev_l:+.3e} of Maxwell (paper: about -{g['vapour_rel_diff_at_T_low']}); "
+          f"extremes {r.min() / rv - 1.0:+.3e} {r.max() / rl - 1.0:+.3e}")
+    assert abs(dev_v - g["vapour_rel_diff_at_T_low"]) < 0.025 and abs(dev_l) < 4e-3
 
 
 def test_oracle_planar_surface_tension_against_paper(oracle_mod):
